@@ -1,0 +1,177 @@
+/*
+ * mpo.h - C ABI of the GB300 noisy-MPO engine.
+ *
+ * The engine simulates 1D brickwork circuits of noisy two-qubit gates on a
+ * density matrix stored as a matrix product operator (MPO), following
+ * Noh, Jiang & Fefferman, "Efficient classical simulation of noisy random
+ * quantum circuits in one dimension" (arXiv:2003.13163):
+ *
+ *   - state: the vectorised density matrix |rho>> of Sec. 3.1 with local
+ *     index I = 2 i + i' (ket digit high, bra digit low), kept as an MPO in
+ *     mixed canonical form (the local QR/TEBD update of the "Note added",
+ *     equivalent in exact arithmetic to the canonical update of App. A);
+ *   - gate: the noisy two-qubit map M = N_2[p] o U of Sec. 3.2 with the
+ *     two-qubit depolarising channel N_2[p] of Sec. 2.2, applied as its
+ *     16x16 superoperator (App. A) to the two-site tensor theta, followed by
+ *     the truncated SVD that keeps the chi_max largest Schmidt values (App. A);
+ *   - output: the MPO entanglement entropy S_l of Sec. 3.3 at every bond after
+ *     every step, Tr rho (Sec. 3.4) and the discarded weight.
+ *
+ * Conventions shared by every call:
+ *   - qubits/sites are 1..n in the paper; the ABI numbers bonds 0..n-2, ABI
+ *     bond b = paper bond l - 1 (the cut between paper sites l and l+1);
+ *   - a gate U is a 4x4 complex128 matrix, row-major, basis index
+ *     2 i_l + i_{l+1} (qubit l is the high digit), stored as interleaved
+ *     (re, im) doubles: double[4][4][2];
+ *   - p is the paper's two-qubit depolarising rate (Sec. 2.2): the channel is
+ *     (1 - 16p/15) rho + (16p/15) (I/4) Tr rho, fully depolarising at p = 15/16;
+ *   - all device work is issued on the stream given to mpo_init. Calls on one
+ *     handle must not run concurrently from several host threads.
+ *
+ * Errors: every int-returning call returns MPO_OK (0) or a negative MPO_ERR_*
+ * code; mpo_last_error() gives a message. After an error the handle refuses
+ * further work with MPO_ERR_STATE until mpo_free. There is no CPU fallback:
+ * without a usable CUDA device mpo_init returns MPO_ERR_CUDA.
+ */
+#ifndef GB300_MPO_H
+#define GB300_MPO_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpo_ctx *mpo_handle;
+
+/* Arithmetic of the path.
+ *   MPO_FP64: complex128 site tensors, every contraction and eigen-solve in FP64
+ *             (the plain form).
+ *   MPO_FP32: complex64 site tensors and FP32 contractions and eigen-solves;
+ *             Schmidt-value normalisation, entropy and log-norm stay FP64. */
+typedef enum { MPO_FP64 = 0, MPO_FP32 = 1 } mpo_precision;
+
+/* Which bonds mpo_entropy reports.
+ *   MPO_S_ALL_BONDS: the end-of-step Schmidt sweep computes lambda at every bond.
+ *   MPO_S_CENTRE:    only the centre bond (ABI bond n/2 - 1); other entries NaN. */
+typedef enum { MPO_S_ALL_BONDS = 0, MPO_S_CENTRE = 1 } mpo_entropy_mode;
+
+enum {
+  MPO_OK = 0,
+  MPO_ERR_ARG = -1,     /* invalid argument (sizes, parity, NULL)              */
+  MPO_ERR_CUDA = -2,    /* a CUDA call failed, or no device                    */
+  MPO_ERR_OOM = -3,     /* device allocation failed or exceeded arena_cap_bytes */
+  MPO_ERR_NOCONV = -4,  /* an eigen-solve hit eig_max_sweeps before converging  */
+  MPO_ERR_TIMEOUT = -5, /* a bounded device-side wait gave up                   */
+  MPO_ERR_STATE = -6    /* handle is in an error state or call order is wrong   */
+};
+
+/* Options; pass NULL for the defaults given in brackets. */
+typedef struct {
+  int eig_max_sweeps;       /* cap on Jacobi sweeps per eigen-solve [40]; reaching it -> MPO_ERR_NOCONV */
+  double sv_rel_cutoff;     /* drop Schmidt values lambda <= cutoff * lambda_max at every
+                               factorisation [1e-7 for FP64, 3e-4 for FP32]; <= 0 selects the default */
+  size_t arena_cap_bytes;   /* refuse device allocations above this total [0 = no cap] */
+  mpo_entropy_mode smode;   /* [MPO_S_ALL_BONDS] */
+  double barrier_timeout_s; /* limit of each device-side grid-barrier wait [5.0] */
+} mpo_opts;
+
+/* Fill *o with the defaults. */
+void mpo_default_opts(mpo_opts *o);
+
+/* Create an n-qubit MPO in the product state |0..0><0..0| (Sec. 4.1, initial
+ * lambda = (1,0,..), one-hot Gamma at I = 0).
+ *   out        : receives the handle (set to NULL on failure).
+ *   n_qubits   : even, 2 <= n_qubits <= 4096 (Sec. 2.1 takes n even).
+ *   chi_max    : bond-dimension cap of the truncation (App. A), 1 <= chi_max <= 4096.
+ *   prec       : MPO_FP64 or MPO_FP32.
+ *   cuda_stream: a cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream),
+ *                or NULL for the legacy default stream.
+ *   opts       : NULL for defaults.
+ * Allocates all device memory up front for the worst-case bond dimensions
+ * min(chi_max, 4^b, 4^(n-b)); returns MPO_ERR_OOM if that exceeds the device
+ * or arena_cap_bytes. */
+int mpo_init(mpo_handle *out, int n_qubits, int chi_max, mpo_precision prec,
+             void *cuda_stream, const mpo_opts *opts);
+
+/* Apply one brickwork step (Sec. 2.1, Sec. 4.1): the noisy gates of one layer
+ * in ascending bond order, each followed by its truncation to chi_max, then
+ * the end-of-step Schmidt sweep and entropy reduction.
+ *   parity : 0 = paper bonds 1,3,..,n-1 (odd time step, n/2 gates);
+ *            1 = paper bonds 2,4,..,n-2 (even time step, n/2-1 gates).
+ *   gates  : [n_gates][4][4][2] doubles (complex128 U, see conventions);
+ *            host or device pointer (detected); gate i acts on paper bond
+ *            2 i + 1 + parity. Host memory is copied before the call returns.
+ *   p      : depolarising rates, host or device; p[i * p_stride] for gate i
+ *            (p_stride = 0 applies p[0] to every gate). 0 <= p <= 1.
+ * The call may synchronise the stream (it reads back kept bond dimensions). */
+int mpo_apply_layer(mpo_handle h, int parity, const double *gates, const double *p, int p_stride);
+
+/* Apply one noisy gate on ABI bond b (paper bond b+1) without the end-of-step
+ * sweep; for tests and custom schedules. Same gate / p formats as above. */
+int mpo_apply_gate(mpo_handle h, int bond, const double *gate, double p);
+
+/* Apply a general 16x16 two-site superoperator (row 4*I_l + I_{l+1}, column
+ * 4*J_l + J_{l+1}, App. A convention), complex128 interleaved [16][16][2],
+ * host pointer, on ABI bond b. Sec. 2.2 notes the method covers any
+ * two-qubit error model; this entry takes the map directly. */
+int mpo_apply_superop(mpo_handle h, int bond, const double *M);
+
+/* Run the Schmidt sweep now (normally done at the end of mpo_apply_layer). */
+int mpo_sweep(mpo_handle h);
+
+/* Read the results of the last step. Synchronises the stream.
+ *   S         : host [n-1]: MPO entanglement entropy (Sec. 3.3, base 2) at ABI
+ *               bond b (NaN where not computed).
+ *   trace     : nullable; Tr rho (Sec. 3.4) including the tracked log-norm.
+ *   discarded : nullable; sum over the step's gates of the discarded weight
+ *               w = sum_{dropped} lambda'^2 / sum_all lambda'^2. */
+int mpo_entropy(mpo_handle h, double *S, double *trace, double *discarded);
+
+/* Schmidt values lambda^[b] of ABI bond b from the last sweep, normalised so
+ * that sum lambda^2 = 1, descending. lam: host [chi_max]; *len receives the
+ * count. */
+int mpo_schmidt(mpo_handle h, int bond, double *lam, int *len);
+
+/* Current bond dimensions: dims host [n+1], dims[0] = dims[n] = 1. */
+int mpo_bond_dims(mpo_handle h, int *dims);
+
+/* Copy site k (0-based) to host as complex128 interleaved [chiL][4][chiR][2],
+ * scaled so that the MPO's product of sites equals rho (the log-norm is
+ * folded into the centre site). *chiL / *chiR receive the dims; buf may be
+ * NULL to query them. */
+int mpo_get_site(mpo_handle h, int k, double *buf, int *chiL, int *chiR);
+
+/* Contract the MPO into |rho>> (4^n complex128, interleaved, index
+ * I_1 I_2 .. I_n with I_1 most significant). n <= 12. Test export. */
+int mpo_to_dense(mpo_handle h, double *rho_vec);
+
+/* Orthogonality-centre site (0-based). */
+int mpo_centre(mpo_handle h, int *centre);
+
+/* Device bytes held by the handle. */
+size_t mpo_device_bytes(mpo_handle h);
+
+/* Release everything; NULL is a no-op. */
+void mpo_free(mpo_handle h);
+
+/* Message of the last error on h (or of the last failed mpo_init when h is
+ * NULL); thread-local storage, valid until the next call. */
+const char *mpo_last_error(mpo_handle h);
+
+/* Stand-alone Hermitian eigen-solver used by the path (cyclic parallel
+ * Jacobi), exported for tests: A is m x m complex (interleaved, row-major,
+ * leading dimension m), device pointer, overwritten. On return w (device,
+ * [m]) holds eigenvalues and V (device, m x m row-major) the eigenvectors as
+ * columns, unsorted. prec selects FP64 (double) or FP32 (float) buffers.
+ * Returns MPO_ERR_NOCONV when max_sweeps is reached. */
+int mpo_eigh(int m, void *A, void *w, void *V, mpo_precision prec, int max_sweeps, void *cuda_stream);
+
+/* Library version string. */
+const char *mpo_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_MPO_H */
