@@ -61,16 +61,17 @@ enum {
   MPO_ERR_ARG = -1,     /* invalid argument (sizes, parity, NULL)              */
   MPO_ERR_CUDA = -2,    /* a CUDA call failed, or no device                    */
   MPO_ERR_OOM = -3,     /* device allocation failed or exceeded arena_cap_bytes */
-  MPO_ERR_NOCONV = -4,  /* an eigen-solve hit eig_max_sweeps before converging  */
+  MPO_ERR_NOCONV = -4,  /* an SVD / eigen-solve hit its sweep cap unconverged   */
   MPO_ERR_TIMEOUT = -5, /* a bounded device-side wait gave up                   */
   MPO_ERR_STATE = -6    /* handle is in an error state or call order is wrong   */
 };
 
 /* Options; pass NULL for the defaults given in brackets. */
 typedef struct {
-  int eig_max_sweeps;       /* cap on Jacobi sweeps per eigen-solve [40]; reaching it -> MPO_ERR_NOCONV */
+  int eig_max_sweeps;       /* cap on Jacobi sweeps per SVD [40, at most 64]; reaching it -> MPO_ERR_NOCONV */
   double sv_rel_cutoff;     /* drop Schmidt values lambda <= cutoff * lambda_max at every
-                               factorisation [1e-7 for FP64, 3e-4 for FP32]; <= 0 selects the default */
+                               factorisation [1e-12 for FP64, 1e-6 for FP32: the rounding
+                               floor of the one-sided Jacobi SVD]; <= 0 selects the default */
   size_t arena_cap_bytes;   /* refuse device allocations above this total [0 = no cap] */
   mpo_entropy_mode smode;   /* [MPO_S_ALL_BONDS] */
   double barrier_timeout_s; /* limit of each device-side grid-barrier wait [5.0] */
@@ -166,6 +167,16 @@ const char *mpo_last_error(mpo_handle h);
  * columns, unsorted. prec selects FP64 (double) or FP32 (float) buffers.
  * Returns MPO_ERR_NOCONV when max_sweeps is reached. */
 int mpo_eigh(int m, void *A, void *w, void *V, mpo_precision prec, int max_sweeps, void *cuda_stream);
+
+/* Stand-alone one-sided Jacobi SVD used by every factorisation of the path
+ * (App. A's SVD of B, and the centre moves), exported for tests: X is r x c
+ * complex (interleaved, row-major, leading dimension c), device pointer,
+ * overwritten with U^H X, whose rows are mutually orthogonal. On return w
+ * (device, [r]) holds the squared row norms (the squared singular values of
+ * the input, unsorted) and Ut (device, r x r row-major) the transpose of the
+ * unitary U, so input = U * output. Returns MPO_ERR_NOCONV when max_sweeps
+ * (<= 64) is reached. */
+int mpo_svd(int r, int c, void *X, void *w, void *Ut, mpo_precision prec, int max_sweeps, void *cuda_stream);
 
 /* Library version string. */
 const char *mpo_version(void);

@@ -1,0 +1,572 @@
+// linalg.cuh - dense complex linear algebra of the MPO update, written for
+// one GB300: a tiled SIMT complex GEMM, a persistent cooperative parallel
+// Jacobi eigen-solver for Hermitian matrices, and the single-CTA
+// sort/select/entropy kernel that turns eigenvalues into kept Schmidt values.
+#pragma once
+#include "common.cuh"
+
+// ---------------------------------------------------------------------------
+// Complex GEMM: C (M x N) = alpha * op(A) * op(B), all row-major.
+//   op == 0: plain; op == 1: conjugate transpose.
+//   op(A)(i,k) = A[i*lda + k]      or conj(A[k*lda + i])
+//   op(B)(k,j) = B[k*ldb + j]      or conj(B[j*ldb + k])
+// alpha = alpha_host * (alpha_dev ? *alpha_dev : 1).
+// CTA tile BM x BN, K-slab BK, 256 threads, each thread TM x TN outputs spaced
+// by 16 rows / 16 columns so that shared-memory reads broadcast along rows.
+// ---------------------------------------------------------------------------
+template <typename T, int BM, int BN, int BK>
+__global__ void __launch_bounds__(256) cgemm_kernel(int M, int N, int K,
+    const cplx<T>* __restrict__ A, int lda, int opA,
+    const cplx<T>* __restrict__ B, int ldb, int opB,
+    cplx<T>* __restrict__ C, int ldc, const double* __restrict__ alpha_dev, double alpha_host) {
+  constexpr int TM = BM / 16, TN = BN / 16;
+  __shared__ cplx<T> As[BK][BM];
+  __shared__ cplx<T> Bs[BK][BN];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
+  cplx<T> acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = czero<T>();
+
+  for (int k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+    for (int s = 0; s < (BM * BK) / 256; ++s) {
+      int idx = tid + 256 * s, i, k;
+      cplx<T> v = czero<T>();
+      if (opA == 0) {
+        i = idx / BK; k = idx % BK;
+        if (row0 + i < M && k0 + k < K) v = A[(size_t)(row0 + i) * lda + (k0 + k)];
+      } else {
+        i = idx % BM; k = idx / BM;
+        if (row0 + i < M && k0 + k < K) v = cconj<T>(A[(size_t)(k0 + k) * lda + (row0 + i)]);
+      }
+      As[k][i] = v;
+    }
+#pragma unroll
+    for (int s = 0; s < (BN * BK) / 256; ++s) {
+      int idx = tid + 256 * s, j, k;
+      cplx<T> v = czero<T>();
+      if (opB == 0) {
+        j = idx % BN; k = idx / BN;
+        if (col0 + j < N && k0 + k < K) v = B[(size_t)(k0 + k) * ldb + (col0 + j)];
+      } else {
+        k = idx % BK; j = idx / BK;
+        if (col0 + j < N && k0 + k < K) v = cconj<T>(B[(size_t)(col0 + j) * ldb + (k0 + k)]);
+      }
+      Bs[k][j] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      cplx<T> a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) cfma<T>(acc[i][j], a[i], b[j]);
+    }
+    __syncthreads();
+  }
+  const T alpha = (T)(alpha_host * (alpha_dev ? *alpha_dev : 1.0));
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int r = row0 + ty + 16 * i;
+    if (r >= M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int c = col0 + tx + 16 * j;
+      if (c < N) C[(size_t)r * ldc + c] = cscale<T>(acc[i][j], alpha);
+    }
+  }
+}
+
+template <typename T>
+inline cudaError_t cgemm(cudaStream_t st, int M, int N, int K, const cplx<T>* A, int lda, int opA,
+                         const cplx<T>* B, int ldb, int opB, cplx<T>* C, int ldc,
+                         const double* alpha_dev = nullptr, double alpha_host = 1.0) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  constexpr int BM = 64, BN = 64, BK = 8;
+  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+  if (K <= 0) {  // empty contraction: C = 0
+    for (int r = 0; r < M; ++r) {
+      cudaError_t e = cudaMemsetAsync(C + (size_t)r * ldc, 0, sizeof(cplx<T>) * N, st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  cgemm_kernel<T, BM, BN, BK><<<grid, 256, 0, st>>>(M, N, K, A, lda, opA, B, ldb, opB, C, ldc, alpha_dev, alpha_host);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Parallel cyclic Jacobi eigen-solver for an m x m Hermitian matrix G
+// (row-major, leading dimension m), in place: on exit G is diagonal to
+// within the stopping rule, w[i] = G_ii and V (row-major) holds the
+// eigenvectors as columns, G_in = V diag(w) V^H.
+//
+// Ordering: round-robin (circle method) over N = m + (m odd) players, so each
+// round rotates N/2 disjoint pairs (p, q) and a sweep of N-1 rounds visits
+// every pair once; an odd m gives one pair a bye per round.
+// Rotation of pair (p, q) with a = G_pp, b = G_qq, g = G_pq = |g| u:
+//   zeta = (b - a) / (2|g|), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
+//   c = 1/sqrt(1 + t^2), s = t c, J = [[c, s], [-conj(u) s, conj(u) c]],
+// the complex form of the symmetric Schur rotation (Golub & Van Loan,
+// Matrix Computations, Sec. 8.5); J^H G J zeroes G_pq.
+// A pair is skipped when |g| <= max(tol_rel sqrt(|a b|), floor_rel max_i|G_ii|)
+// (the relative criterion of Demmel & Veselic 1992 plus an absolute floor at
+// the rounding level of the input). The solve stops after a sweep without a
+// rotation; status = 1 if max_sweeps is reached first.
+//
+// Each round runs as three phases of one persistent cooperative launch:
+//   A (every CTA, redundantly): the rotation table of the round -> smem;
+//   B (G <- G J, V <- V J): one warp per row, lanes over pairs;   barrier
+//   C (G <- J^H G): one warp per pair, lanes over columns;           barrier
+// All G/V traffic uses L2-only loads/stores because other CTAs write it.
+// ---------------------------------------------------------------------------
+template <typename T> struct JRot { T c, s, ur, ui; };
+
+__device__ __forceinline__ int rr_player(int pos, int r, int N) {
+  return pos == 0 ? 0 : 1 + ((pos - 1 + r) % (N - 1));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) jacobi_kernel(cplx<T>* G, int m, cplx<T>* V, T* w, GridCtl* ctl,
+                                                      int max_sweeps, T tol_rel, T floor_rel, long long timeout_ns) {
+  extern __shared__ unsigned char jsmem[];
+  JRot<T>* rot = reinterpret_cast<JRot<T>*>(jsmem);
+  __shared__ int s_active;
+  __shared__ T s_red[32];
+  const int N = m + (m & 1), npairs = N / 2;
+  const unsigned nblk = gridDim.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarp_blk = blockDim.x >> 5;
+  const long gwarp = (long)blockIdx.x * nwarp_blk + warp, nwarps = (long)nblk * nwarp_blk;
+  const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x, gthreads = (size_t)nblk * blockDim.x;
+
+  // V = I
+  for (size_t e = gtid; e < (size_t)m * m; e += gthreads) {
+    size_t r = e / m, c = e % m;
+    stcg(&V[e], mk<T>(r == c ? T(1) : T(0), T(0)));
+  }
+  // scale = max_i |G_ii| (each CTA redundantly)
+  T loc = T(0);
+  for (int i = threadIdx.x; i < m; i += blockDim.x) loc = fmax(loc, fabs(ldcg(&G[(size_t)i * m + i]).x));
+  for (int o = 16; o > 0; o >>= 1) loc = fmax(loc, __shfl_xor_sync(0xffffffffu, loc, o));
+  if (lane == 0) s_red[warp] = loc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T mx = T(0);
+    for (int i = 0; i < nwarp_blk; ++i) mx = fmax(mx, s_red[i]);
+    s_red[0] = mx;
+  }
+  __syncthreads();
+  const T floor_abs = floor_rel * s_red[0];
+  if (!grid_barrier(ctl, nblk, timeout_ns)) return;
+
+  int sweep = 0;
+  bool converged = (m <= 1);
+  for (; sweep < max_sweeps && !converged; ++sweep) {
+    long sweep_active = 0;
+    for (int r = 0; r < N - 1; ++r) {
+      // ---- phase A: rotation table -------------------------------------
+      if (threadIdx.x == 0) s_active = 0;
+      __syncthreads();
+      int my_active = 0;
+      for (int pi = threadIdx.x; pi < npairs; pi += blockDim.x) {
+        int p = rr_player(pi, r, N), q = rr_player(N - 1 - pi, r, N);
+        if (p > q) { int t_ = p; p = q; q = t_; }
+        JRot<T> R; R.c = T(1); R.s = T(0); R.ur = T(1); R.ui = T(0);
+        if (q < m) {
+          const T a = ldcg(&G[(size_t)p * m + p]).x, b = ldcg(&G[(size_t)q * m + q]).x;
+          const cplx<T> g = ldcg(&G[(size_t)p * m + q]);
+          const T ag = hypot(g.x, g.y);
+          const T thr = fmax(tol_rel * sqrt(fabs(a * b)), floor_abs);
+          if (ag > thr && ag > T(0)) {
+            const T zeta = (b - a) / (T(2) * ag);
+            T t;
+            if (fabs(zeta) > T(1) / eps_of<T>::value) t = T(0.5) / zeta;
+            else t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+            const T c = T(1) / sqrt(T(1) + t * t);
+            R.c = c; R.s = t * c; R.ur = g.x / ag; R.ui = g.y / ag;
+            if (R.s != T(0)) ++my_active;
+          }
+        }
+        rot[pi] = R;
+      }
+      if (my_active) atomicAdd(&s_active, my_active);
+      __syncthreads();
+      const int act = s_active;   // identical in every CTA: same inputs, same code
+      sweep_active += act;
+      if (act == 0) continue;
+      // ---- phase B: column rotations, G <- G J and V <- V J ---------------
+      for (long row = gwarp; row < 2L * m; row += nwarps) {
+        cplx<T>* Rw = row < m ? G + (size_t)row * m : V + (size_t)(row - m) * m;
+        for (int pi = lane; pi < npairs; pi += 32) {
+          const JRot<T> R = rot[pi];
+          if (R.s == T(0)) continue;
+          int p = rr_player(pi, r, N), q = rr_player(N - 1 - pi, r, N);
+          if (p > q) { int t_ = p; p = q; q = t_; }
+          const cplx<T> x = ldcg(&Rw[p]), y = ldcg(&Rw[q]);
+          const cplx<T> uy = cmul<T>(mk<T>(R.ur, -R.ui), y);   // conj(u) y
+          stcg(&Rw[p], mk<T>(R.c * x.x - R.s * uy.x, R.c * x.y - R.s * uy.y));
+          stcg(&Rw[q], mk<T>(R.s * x.x + R.c * uy.x, R.s * x.y + R.c * uy.y));
+        }
+      }
+      if (!grid_barrier(ctl, nblk, timeout_ns)) return;
+      // ---- phase C: row rotations, G <- J^H G ----------------------------
+      for (long pi = gwarp; pi < npairs; pi += nwarps) {
+        const JRot<T> R = rot[pi];
+        if (R.s == T(0)) continue;
+        int p = rr_player((int)pi, r, N), q = rr_player(N - 1 - (int)pi, r, N);
+        if (p > q) { int t_ = p; p = q; q = t_; }
+        cplx<T>* Rp = G + (size_t)p * m;
+        cplx<T>* Rq = G + (size_t)q * m;
+        for (int j = lane; j < m; j += 32) {
+          const cplx<T> x = ldcg(&Rp[j]), y = ldcg(&Rq[j]);
+          const cplx<T> uy = cmul<T>(mk<T>(R.ur, R.ui), y);    // u y
+          cplx<T> np_ = mk<T>(R.c * x.x - R.s * uy.x, R.c * x.y - R.s * uy.y);
+          cplx<T> nq_ = mk<T>(R.s * x.x + R.c * uy.x, R.s * x.y + R.c * uy.y);
+          if (j == q) np_ = czero<T>();
+          if (j == p) { nq_ = czero<T>(); np_.y = T(0); }
+          if (j == q) nq_.y = T(0);
+          stcg(&Rp[j], np_);
+          stcg(&Rq[j], nq_);
+        }
+      }
+      if (!grid_barrier(ctl, nblk, timeout_ns)) return;
+    }
+    if (sweep_active == 0) converged = true;
+  }
+  for (size_t i = gtid; i < (size_t)m; i += gthreads) w[i] = ldcg(&G[i * m + i]).x;
+  if (gtid == 0) {
+    ctl->sweeps = sweep;
+    ctl->status = converged ? 0 : 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Select kernel (one CTA): turn the m eigenvalues w of a Gram matrix (the
+// squared Schmidt values lambda'^2 of the factorised bond) into the kept set.
+//   - bitonic sort of (value desc, index asc) in shared memory (stable order
+//     for exact ties), negative rounding values clamped to 0;
+//   - k = min(cap, #{lambda^2 > cutoff^2 * lambda_max^2}), at least 1;
+//   - sums in FP64: total = sum lambda^2, kept = sum of the k largest;
+//   - outputs perm[0..k), lam2[0..k) (descending), info->k, info->kept,
+//     info->total; adds (total-kept)/total to *disc_acc and 0.5 log(kept) to
+//     *lognorm when those are non-null;
+//   - with S_out: the MPO entanglement entropy -sum p log2 p, p = lam2/kept
+//     (Sec. 3.3), and the normalised lam2/kept into schmidt_out.
+// ---------------------------------------------------------------------------
+struct SelectInfo {
+  int k;
+  int status;
+  int pad[2];
+  double kept;
+  double total;
+  double inv_sqrt_kept;
+  double pad2;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(1024) select_kernel(const T* __restrict__ w, int m, int cap, double cutoff2,
+                                                       int* __restrict__ perm, double* __restrict__ lam2,
+                                                       SelectInfo* info, double* disc_acc, double* lognorm,
+                                                       double* S_out, double* schmidt_out) {
+  extern __shared__ unsigned char ssm[];
+  int P = 1;
+  while (P < m) P <<= 1;
+  double* key = reinterpret_cast<double*>(ssm);
+  int* idx = reinterpret_cast<int*>(key + P);
+  __shared__ double red[32];
+  __shared__ double s_tot, s_kept, s_max;
+  __shared__ int s_k;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wp = tid >> 5;
+  for (int i = tid; i < P; i += nt) {
+    if (i < m) { double v = (double)w[i]; key[i] = v > 0.0 ? v : 0.0; idx[i] = i; }
+    else { key[i] = -1.0; idx[i] = 0x7fffffff; }
+  }
+  __syncthreads();
+  // bitonic sort, descending by key, ascending index on ties
+  for (int size = 2; size <= P; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = tid; i < P; i += nt) {
+        int j = i ^ stride;
+        if (j > i) {
+          bool desc = ((i & size) == 0);
+          double ki = key[i], kj = key[j];
+          int ii = idx[i], ij = idx[j];
+          bool i_first = (ki > kj) || (ki == kj && ii < ij);   // i belongs before j in descending order
+          bool swap = desc ? !i_first : i_first;
+          if (swap) { key[i] = kj; key[j] = ki; idx[i] = ij; idx[j] = ii; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // total and max
+  double loc = 0.0;
+  for (int i = tid; i < m; i += nt) loc += key[i];
+  for (int o = 16; o > 0; o >>= 1) loc += __shfl_xor_sync(0xffffffffu, loc, o);
+  if (lane == 0) red[wp] = loc;
+  __syncthreads();
+  if (tid == 0) {
+    double s = 0.0;
+    for (int i = 0; i < (nt + 31) / 32; ++i) s += red[i];
+    s_tot = s;
+    s_max = key[0];
+    const double thr = cutoff2 * key[0];
+    int k = 0;
+    const int lim = cap < m ? cap : m;
+    while (k < lim && key[k] > thr) ++k;
+    if (k == 0) k = 1;
+    s_k = k;
+  }
+  __syncthreads();
+  const int k = s_k;
+  loc = 0.0;
+  for (int i = tid; i < k; i += nt) loc += key[i];
+  for (int o = 16; o > 0; o >>= 1) loc += __shfl_xor_sync(0xffffffffu, loc, o);
+  __syncthreads();
+  if (lane == 0) red[wp] = loc;
+  __syncthreads();
+  if (tid == 0) {
+    double s = 0.0;
+    for (int i = 0; i < (nt + 31) / 32; ++i) s += red[i];
+    s_kept = s;
+  }
+  __syncthreads();
+  const double kept = s_kept;
+  for (int i = tid; i < k; i += nt) { perm[i] = idx[i]; lam2[i] = key[i]; }
+  if (S_out) {
+    loc = 0.0;
+    for (int i = tid; i < k; i += nt) {
+      const double pz = kept > 0.0 ? key[i] / kept : 0.0;
+      if (schmidt_out) schmidt_out[i] = pz;
+      if (pz > 0.0) loc -= pz * log2(pz);
+    }
+    for (int o = 16; o > 0; o >>= 1) loc += __shfl_xor_sync(0xffffffffu, loc, o);
+    __syncthreads();
+    if (lane == 0) red[wp] = loc;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0.0;
+      for (int i = 0; i < (nt + 31) / 32; ++i) s += red[i];
+      *S_out = s;
+    }
+  }
+  if (tid == 0) {
+    info->k = k;
+    info->kept = kept;
+    info->total = s_tot;
+    info->inv_sqrt_kept = kept > 0.0 ? 1.0 / sqrt(kept) : 0.0;
+    if (disc_acc && s_tot > 0.0) *disc_acc += (s_tot - kept) / s_tot;
+    if (lognorm && kept > 0.0) *lognorm += 0.5 * log(kept);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Gather selected eigenvector columns with a per-column scale.
+//   transpose_conj == 0: out[r*ldo + j] = V[r*ldv + perm[j]] * f_j
+//   transpose_conj == 1: out[j*ldo + r] = conj(V[r*ldv + perm[j]]) * f_j
+// f_j by mode: 0 -> 1; 1 -> 1/sqrt(lam2_j); 2 -> sqrt(lam2_j / kept);
+//              3 -> sqrt(lam2_j).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void gather_kernel(const cplx<T>* __restrict__ V, int ldv, const int* __restrict__ perm,
+                              const double* __restrict__ lam2, const SelectInfo* __restrict__ info,
+                              int rows, int k_cap, int transpose_conj, int mode, cplx<T>* __restrict__ out, int ldo) {
+  const int k = info->k < k_cap ? info->k : k_cap;
+  const size_t total = (size_t)rows * k;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    int r, j;
+    if (transpose_conj) { j = (int)(e / rows); r = (int)(e % rows); }
+    else { r = (int)(e / k); j = (int)(e % k); }
+    double f = 1.0;
+    if (mode == 1) f = lam2[j] > 0.0 ? 1.0 / sqrt(lam2[j]) : 0.0;
+    else if (mode == 2) f = info->kept > 0.0 ? sqrt(lam2[j] / info->kept) : 0.0;
+    else if (mode == 3) f = sqrt(lam2[j]);
+    cplx<T> v = V[(size_t)r * ldv + perm[j]];
+    if (transpose_conj) out[(size_t)j * ldo + r] = cscale<T>(cconj<T>(v), (T)f);
+    else out[(size_t)r * ldo + j] = cscale<T>(v, (T)f);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One-sided (Hestenes) Jacobi SVD by row orthogonalisation.
+// Input X (r x c, row-major, leading dimension ldx), in place. On exit the
+// rows of X are mutually orthogonal, X_out = U^H X_in with U unitary (r x r),
+// returned transposed as Ut (row p of Ut = column p of U, leading dim r), and
+// w[i] = ||row i of X_out||^2: X_in = U X_out, so the squared singular values
+// of X_in are w and its left singular vectors the columns of U
+// (Hestenes 1958; Demmel & Veselic 1992 for the relative-accuracy stopping
+// rule). No Gram matrix is formed, so small singular values keep their
+// relative accuracy instead of being lost below eps * sigma_max^2.
+//
+// Pair (p, q) with a = ||x_p||^2, b = ||x_q||^2, g = <x_p, x_q> = sum_j
+// x_p[j] conj(x_q[j]) is rotated by the same J as in the two-sided solver:
+// rows  x_p <- c x_p - u s x_q,   x_q <- s x_p + u c x_q      (X <- J^H X)
+// Ut    t_p <- c t_p - u* s t_q,  t_q <- s t_p + u* c t_q      (U <- U J)
+// Ordering is round-robin as above; pairs of one round touch disjoint rows,
+// so a round is one phase (one warp per pair) followed by one grid barrier.
+// A sweep with no rotation (|g| <= max(tol sqrt(ab), floor)) ends the solve.
+// ---------------------------------------------------------------------------
+struct OSCtl {
+  GridCtl g;
+  int active[64];   // rotations per sweep (grid-wide atomic counts)
+  double scale;
+  double pad;
+};
+
+template <typename T>
+__device__ __forceinline__ void warp_sum3(T& a, T& b, T& c, T& d) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+    d += __shfl_xor_sync(0xffffffffu, d, o);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) onesided_jacobi_kernel(cplx<T>* X, int r, int c, int ldx, cplx<T>* Ut, T* w,
+                                                               OSCtl* ctl, int max_sweeps, T tol_rel, T floor_rel,
+                                                               long long timeout_ns) {
+  const int N = r + (r & 1), npairs = N / 2;
+  const unsigned nblk = gridDim.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwb = blockDim.x >> 5;
+  const long gwarp = (long)blockIdx.x * nwb + warp, nwarps = (long)nblk * nwb;
+  const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x, gthreads = (size_t)nblk * blockDim.x;
+  if (max_sweeps > 64) max_sweeps = 64;
+
+  for (size_t e = gtid; e < (size_t)r * r; e += gthreads) {
+    const size_t i = e / r, j = e % r;
+    stcg(&Ut[e], mk<T>(i == j ? T(1) : T(0), T(0)));
+  }
+  // squared row norms -> w, then the largest one sets the absolute floor
+  for (long i = gwarp; i < r; i += nwarps) {
+    T s = T(0);
+    for (int j = lane; j < c; j += 32) { const cplx<T> x = ldcg(&X[(size_t)i * ldx + j]); s += x.x * x.x + x.y * x.y; }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) w[i] = s;
+  }
+  if (!grid_barrier(&ctl->g, nblk, timeout_ns)) return;
+  __shared__ T s_floor;
+  if (threadIdx.x == 0) {
+    T mx = T(0);
+    for (int i = 0; i < r; ++i) mx = fmax(mx, __ldcg(&w[i]));
+    s_floor = floor_rel * mx;
+  }
+  __syncthreads();
+  const T floor_abs = s_floor;
+
+  int sweep = 0;
+  bool converged = (r <= 1);
+  for (; sweep < max_sweeps && !converged; ++sweep) {
+    for (int rd = 0; rd < N - 1; ++rd) {
+      for (long pi = gwarp; pi < npairs; pi += nwarps) {
+        int p = rr_player((int)pi, rd, N), q = rr_player(N - 1 - (int)pi, rd, N);
+        if (p > q) { int t_ = p; p = q; q = t_; }
+        if (q >= r) continue;
+        cplx<T>* xp = X + (size_t)p * ldx;
+        cplx<T>* xq = X + (size_t)q * ldx;
+        T a = T(0), b = T(0), gr = T(0), gi = T(0);
+        for (int j = lane; j < c; j += 32) {
+          const cplx<T> x = ldcg(&xp[j]), y = ldcg(&xq[j]);
+          a = fma(x.x, x.x, fma(x.y, x.y, a));
+          b = fma(y.x, y.x, fma(y.y, y.y, b));
+          gr = fma(x.x, y.x, fma(x.y, y.y, gr));     // x conj(y)
+          gi = fma(x.y, y.x, fma(-x.x, y.y, gi));
+        }
+        warp_sum3<T>(a, b, gr, gi);
+        const T ag = hypot(gr, gi);
+        const T thr = fmax(tol_rel * sqrt(a * b), floor_abs);
+        if (!(ag > thr) || ag == T(0)) continue;
+        const T zeta = (b - a) / (T(2) * ag);
+        T t;
+        if (fabs(zeta) > T(1) / eps_of<T>::value) t = T(0.5) / zeta;
+        else t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+        const T cs = T(1) / sqrt(T(1) + t * t), sn = t * cs;
+        if (sn == T(0)) continue;
+        const T ur = gr / ag, ui = gi / ag;
+        if (lane == 0) atomicAdd(&ctl->active[sweep], 1);
+        for (int j = lane; j < c; j += 32) {
+          const cplx<T> x = ldcg(&xp[j]), y = ldcg(&xq[j]);
+          const cplx<T> uy = cmul<T>(mk<T>(ur, ui), y);
+          stcg(&xp[j], mk<T>(cs * x.x - sn * uy.x, cs * x.y - sn * uy.y));
+          stcg(&xq[j], mk<T>(sn * x.x + cs * uy.x, sn * x.y + cs * uy.y));
+        }
+        cplx<T>* tp = Ut + (size_t)p * r;
+        cplx<T>* tq = Ut + (size_t)q * r;
+        for (int j = lane; j < r; j += 32) {
+          const cplx<T> x = ldcg(&tp[j]), y = ldcg(&tq[j]);
+          const cplx<T> uy = cmul<T>(mk<T>(ur, -ui), y);
+          stcg(&tp[j], mk<T>(cs * x.x - sn * uy.x, cs * x.y - sn * uy.y));
+          stcg(&tq[j], mk<T>(sn * x.x + cs * uy.x, sn * x.y + cs * uy.y));
+        }
+      }
+      if (!grid_barrier(&ctl->g, nblk, timeout_ns)) return;
+    }
+    if (atomicAdd(&ctl->active[sweep], 0) == 0) converged = true;
+  }
+  for (long i = gwarp; i < r; i += nwarps) {
+    T s = T(0);
+    for (int j = lane; j < c; j += 32) { const cplx<T> x = ldcg(&X[(size_t)i * ldx + j]); s += x.x * x.x + x.y * x.y; }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) w[i] = s;
+  }
+  if (gtid == 0) {
+    ctl->g.sweeps = sweep;
+    ctl->g.status = converged ? 0 : 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Gather of selected rows: element (j, i) = f_j * op(src[perm[j] * lds + i]),
+// i < len, j < k (k = min(info->k, k_cap)), op = conj if conj_ else identity;
+// written to out[j * ldo + i] (transpose == 0) or out[i * ldo + j] (== 1).
+// f_j by mode: 0 -> 1; 1 -> 1/sqrt(lam2_j); 2 -> sqrt(lam2_j / kept);
+//              3 -> 1/sqrt(kept).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void gather_rows_kernel(const cplx<T>* __restrict__ src, int lds, int len, const int* __restrict__ perm,
+                                  const double* __restrict__ lam2, const SelectInfo* __restrict__ info, int k_cap,
+                                  int transpose, int conj_, int mode, cplx<T>* __restrict__ out, int ldo) {
+  const int k = info->k < k_cap ? info->k : k_cap;
+  const size_t total = (size_t)len * k;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    int i, j;
+    if (transpose) { i = (int)(e / k); j = (int)(e % k); }
+    else { j = (int)(e / len); i = (int)(e % len); }
+    double f = 1.0;
+    if (mode == 1) f = lam2[j] > 0.0 ? 1.0 / sqrt(lam2[j]) : 0.0;
+    else if (mode == 2) f = info->kept > 0.0 ? sqrt(lam2[j] / info->kept) : 0.0;
+    else if (mode == 3) f = info->inv_sqrt_kept;
+    cplx<T> v = src[(size_t)perm[j] * lds + i];
+    if (conj_) v = cconj<T>(v);
+    v = cscale<T>(v, (T)f);
+    if (transpose) out[(size_t)i * ldo + j] = v;
+    else out[(size_t)j * ldo + i] = v;
+  }
+}
+
+// out (c x r) = in (r x c)^H, 32 x 32 tiles through shared memory.
+template <typename T>
+__global__ void conj_transpose_kernel(const cplx<T>* __restrict__ in, int r, int c, int ldi, cplx<T>* __restrict__ out, int ldo) {
+  __shared__ cplx<T> tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+    const int i = by + yy, j = bx + threadIdx.x;
+    if (i < r && j < c) tile[yy][threadIdx.x] = in[(size_t)i * ldi + j];
+  }
+  __syncthreads();
+  for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+    const int j = bx + yy, i = by + threadIdx.x;
+    if (j < c && i < r) out[(size_t)j * ldo + i] = cconj<T>(tile[threadIdx.x][yy]);
+  }
+}

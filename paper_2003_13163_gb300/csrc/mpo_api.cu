@@ -1,0 +1,746 @@
+// mpo_api.cu - the C ABI of include/mpo.h: device store, per-gate update,
+// end-of-step Schmidt sweep and observables of the noisy-MPO simulation of
+// arXiv:2003.13163, on one GB300.
+//
+// State layout (device, one buffer per site, all of the same capacity so that
+// results can be produced in a spare buffer and swapped in by pointer):
+//   site k holds A_k[alpha][I][beta], row-major, chi[k] x 4 x chi[k+1],
+//   complex (double2 or float2). Its left matricisation L(A_k) is the plain
+//   row-major (4 chi[k]) x chi[k+1] matrix, its right matricisation R(A_k) the
+//   plain row-major chi[k] x (4 chi[k+1]) matrix: both are views of the same
+//   memory. Sites left of the centre are left isometries, sites right of it
+//   right isometries; the centre has unit Frobenius norm and the true scale
+//   is exp(lognorm) (device FP64), so rho = exp(lognorm) * A_1 ... A_n.
+//
+// Per noisy gate on sites (i, i+1) (App. A bulk/edge cases, with the local
+// update of the Note added):
+//   1. move the centre to i or i+1 (QR-type moves, below);
+//   2. theta = L(A_i) R(A_{i+1})                       (complex GEMM)
+//   3. theta' = M theta on (I, J)                      (superoperator kernel)
+//   4. Gram of the smaller side, Hermitian eigen-solve (Jacobi), select the
+//      chi_max largest lambda'^2 (App. A truncation), discarded weight;
+//   5. write back: left isometry -> site i, Lambda W^H / ||kept|| -> site i+1.
+// Centre moves and the sweep use the same Gram/eigen route: for the centre C,
+// G = C^H C (or C C^H) = V diag(sigma^2) V^H, the isometry is C V Sigma^-1 (or
+// Sigma^-1 V^H C) and Sigma V^H (or V Sigma) is pushed into the neighbour;
+// sigma <= cutoff * sigma_max are dropped (they are below the rounding floor
+// of the Gram). The sweep's sigma at bond b are the Schmidt values lambda^[b].
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <cmath>
+#include <string>
+#include <vector>
+#include <algorithm>
+#include <type_traits>
+
+#include "../../include/mpo.h"
+#include "common.cuh"
+#include "linalg.cuh"
+#include "mpo_kernels.cuh"
+
+namespace {
+
+thread_local std::string g_last_init_error;
+
+struct HostSync {   // pinned read-back of the last select + eigen-solve
+  SelectInfo info;
+  GridCtl ctl;
+};
+
+}  // namespace
+
+struct mpo_ctx {
+  int n = 0, chi_max = 0;
+  mpo_precision prec = MPO_FP64;
+  cudaStream_t st = nullptr;
+  mpo_opts opts{};
+  double cutoff = 0.0;
+  bool failed = false;
+  std::string msg;
+  int device = 0, num_sms = 0;
+
+  std::vector<int> cap, chi;       // bond caps / current dims, index 0..n
+  std::vector<void*> site;         // n buffers, each site_cap elements
+  void* spare = nullptr;
+  size_t site_cap = 0, esz = 0;    // elements per site buffer, bytes per complex
+  void* theta2 = nullptr;          // conjugate-transposed operand of the one-sided SVD
+  void *theta = nullptr, *vecs = nullptr, *tmp = nullptr, *wv = nullptr, *Ms = nullptr;
+  size_t theta_cap = 0, tmp_cap = 0;
+  int m_cap = 0;
+  int* perm = nullptr;
+  double* lam2 = nullptr;
+  SelectInfo* info = nullptr;
+  GridCtl* ctl = nullptr;
+  OSCtl* osctl = nullptr;
+  double* scal = nullptr;          // [0] lognorm, [1] discarded accumulator
+  double* dS = nullptr;            // [n-1]
+  double* dschmidt = nullptr;      // [(n-1) * chi_max]
+  double2* dgates = nullptr;
+  double2* dsup = nullptr;         // staging of a caller-given 16x16 superoperator
+  double* dp = nullptr;
+  double2 *tv0 = nullptr, *tv1 = nullptr;
+  HostSync* hs = nullptr;          // pinned
+  std::vector<int> schmidt_len;
+  std::vector<char> s_valid;
+  int centre = 0;
+  size_t bytes = 0;
+  int last_sweeps = 0;
+};
+
+// ------------------------------------------------------------------ errors --
+static int fail(mpo_ctx* h, int code, const std::string& m) {
+  h->failed = true;
+  h->msg = m;
+  return code;
+}
+#define CK(h, call)                                                                         \
+  do {                                                                                      \
+    cudaError_t e__ = (call);                                                               \
+    if (e__ != cudaSuccess)                                                                 \
+      return fail((h), MPO_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e__)); \
+  } while (0)
+
+static int cap_of(int b, int n, int chi_max) {
+  // min(chi_max, 4^b, 4^(n-b)) without overflow
+  int e = std::min(b, n - b);
+  long long v = 1;
+  for (int i = 0; i < e && v < chi_max; ++i) v *= 4;
+  return (int)std::min<long long>(v, chi_max);
+}
+
+// ------------------------------------------------------- eigen-solve launch --
+template <typename T>
+static cudaError_t launch_jacobi(cudaStream_t st, cplx<T>* G, int m, cplx<T>* V, T* w, GridCtl* ctl,
+                                 int max_sweeps, double timeout_s, int num_sms) {
+  const int N = m + (m & 1);
+  const size_t smem = sizeof(JRot<T>) * (size_t)std::max(1, N / 2);
+  cudaError_t e = cudaFuncSetAttribute(jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel<T>, 256, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int coresident = per_sm * num_sms;
+  int want = (2 * m + 7) / 8;   // one warp per row of G and V in phase B
+  int blocks = std::max(1, std::min(coresident, want));
+  e = cudaMemsetAsync(ctl, 0, sizeof(GridCtl), st);
+  if (e != cudaSuccess) return e;
+  const T tol_rel = std::is_same<T, double>::value ? (T)1e-14 : (T)2e-6;
+  const T floor_rel = eps_of<T>::value;
+  long long timeout_ns = (long long)(timeout_s * 1e9);
+  void* args[] = {&G, &m, &V, &w, &ctl, &max_sweeps, (void*)&tol_rel, (void*)&floor_rel, &timeout_ns};
+  return cudaLaunchCooperativeKernel((const void*)jacobi_kernel<T>, dim3(blocks), dim3(256), args, smem, st);
+}
+
+template <typename T>
+static cudaError_t launch_select(cudaStream_t st, const T* w, int m, int cap, double cutoff2, int* perm,
+                                 double* lam2, SelectInfo* info, double* disc, double* lognorm, double* S,
+                                 double* sch) {
+  int P = 1;
+  while (P < m) P <<= 1;
+  const size_t smem = (size_t)P * (sizeof(double) + sizeof(int));
+  cudaError_t e = cudaFuncSetAttribute(select_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  select_kernel<T><<<1, 1024, smem, st>>>(w, m, cap, cutoff2, perm, lam2, info, disc, lognorm, S, sch);
+  return cudaGetLastError();
+}
+
+static int grid_for(size_t work, int num_sms) {
+  size_t b = (work + 255) / 256;
+  size_t mx = (size_t)num_sms * 16;
+  return (int)std::max<size_t>(1, std::min(b, mx));
+}
+
+template <typename T>
+static cudaError_t launch_onesided(cudaStream_t st, cplx<T>* X, int r, int c, int ldx, cplx<T>* Ut, T* w, OSCtl* ctl,
+                                   int max_sweeps, double timeout_s, int num_sms) {
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, onesided_jacobi_kernel<T>, 256, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int N = r + (r & 1);
+  const int want = std::max(1, (N / 2 + 7) / 8);   // one warp per pair
+  const int blocks = std::max(1, std::min(per_sm * num_sms, want));
+  e = cudaMemsetAsync(ctl, 0, sizeof(OSCtl), st);
+  if (e != cudaSuccess) return e;
+  // rows count as orthogonal once |<x_p, x_q>| <= 2 eps sqrt(c) ||x_p|| ||x_q||,
+  // the rounding level of the length-c dot product itself
+  const T tol_rel = (T)(2.0 * eps_of<T>::value * std::sqrt((double)std::max(c, 1)));
+  const T floor_rel = eps_of<T>::value * eps_of<T>::value;
+  long long timeout_ns = (long long)(timeout_s * 1e9);
+  void* args[] = {&X, &r, &c, &ldx, &Ut, &w, &ctl, &max_sweeps, (void*)&tol_rel, (void*)&floor_rel, &timeout_ns};
+  return cudaLaunchCooperativeKernel((const void*)onesided_jacobi_kernel<T>, dim3(blocks), dim3(256), args, 0, st);
+}
+
+// One-sided Jacobi SVD of X (r x c, rows orthogonalised in place; left factor
+// transposed in h->vecs), then select the kept squared singular values; waits
+// for the stream and returns the kept count in *k (or an error code).
+template <typename T>
+static int svd_select(mpo_ctx* h, cplx<T>* X, int r, int c, int ldx, int cap, bool disc, double* S, double* sch, int* k) {
+  T* w = (T*)h->wv;
+  CK(h, launch_onesided<T>(h->st, X, r, c, ldx, (cplx<T>*)h->vecs, w, h->osctl, h->opts.eig_max_sweeps,
+                           h->opts.barrier_timeout_s, h->num_sms));
+  CK(h, launch_select<T>(h->st, w, r, cap, h->cutoff * h->cutoff, h->perm, h->lam2, h->info,
+                         disc ? h->scal + 1 : nullptr, h->scal, S, sch));
+  CK(h, cudaMemcpyAsync(&h->hs->info, h->info, sizeof(SelectInfo), cudaMemcpyDeviceToHost, h->st));
+  CK(h, cudaMemcpyAsync(&h->hs->ctl, &h->osctl->g, sizeof(GridCtl), cudaMemcpyDeviceToHost, h->st));
+  CK(h, cudaStreamSynchronize(h->st));
+  if (h->hs->ctl.err) return fail(h, MPO_ERR_TIMEOUT, "grid barrier wait timed out in the SVD");
+  h->last_sweeps = h->hs->ctl.sweeps;
+  if (h->hs->ctl.status)
+    return fail(h, MPO_ERR_NOCONV, "Jacobi SVD reached eig_max_sweeps (" + std::to_string(r) + " x " + std::to_string(c) + ")");
+  *k = h->hs->info.k;
+  return MPO_OK;
+}
+
+template <typename T> static cplx<T>* S_(mpo_ctx* h, int k) { return (cplx<T>*)h->site[k]; }
+
+static void swap_spare(mpo_ctx* h, int k) { std::swap(h->site[k], h->spare); }
+
+template <typename T>
+static cudaError_t gather_rows(mpo_ctx* h, const cplx<T>* src, int lds, int len, int k, int transpose, int conj_,
+                               int mode, cplx<T>* out, int ldo) {
+  gather_rows_kernel<T><<<grid_for((size_t)len * k, h->num_sms), 256, 0, h->st>>>(
+      src, lds, len, h->perm, h->lam2, h->info, k, transpose, conj_, mode, out, ldo);
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t conj_transpose(mpo_ctx* h, const cplx<T>* in, int r, int c, int ldi, cplx<T>* out, int ldo) {
+  dim3 grid((c + 31) / 32, (r + 31) / 32);
+  conj_transpose_kernel<T><<<grid, dim3(32, 8), 0, h->st>>>(in, r, c, ldi, out, ldo);
+  return cudaGetLastError();
+}
+
+// Centre at site k -> site k becomes a left isometry, centre moves to k+1.
+// L(C) = Y^H with Y = U X' (one-sided SVD of Y): Q = X'^H Sigma^-1 -> site k,
+// R = Sigma U^H / ||kept|| pushed into site k+1.
+template <typename T>
+static int move_right(mpo_ctx* h, int k) {
+  const int mX = 4 * h->chi[k], r = h->chi[k + 1], mR = 4 * h->chi[k + 2];
+  cplx<T>* Y = (cplx<T>*)h->theta2;
+  cplx<T>* tmp = (cplx<T>*)h->tmp;
+  CK(h, conj_transpose<T>(h, S_<T>(h, k), mX, r, r, Y, mX));                   // Y = L(C)^H (r x mX)
+  int rk = 0;
+  int rc = svd_select<T>(h, Y, r, mX, mX, r, false, nullptr, nullptr, &rk);
+  if (rc) return rc;
+  CK(h, gather_rows<T>(h, Y, mX, mX, rk, 1, 1, 1, (cplx<T>*)h->spare, rk));     // Q (mX x rk)
+  swap_spare(h, k);
+  CK(h, gather_rows<T>(h, (cplx<T>*)h->vecs, r, r, rk, 0, 1, 2, tmp, r));         // R (rk x r)
+  CK(h, cgemm<T>(h->st, rk, mR, r, tmp, r, 0, S_<T>(h, k + 1), mR, 0, (cplx<T>*)h->spare, mR));
+  swap_spare(h, k + 1);
+  h->chi[k + 1] = rk;
+  h->centre = k + 1;
+  return MPO_OK;
+}
+
+// Centre at site k -> site k becomes a right isometry, centre moves to k-1.
+// R(C) = U X' (one-sided SVD in place): Lambda^-1 X' -> site k,
+// U Lambda / ||kept|| pushed into site k-1. The row norms of X' are the
+// Schmidt values of bond k; with record they and the entropy are stored.
+template <typename T>
+static int move_left(mpo_ctx* h, int k, bool record) {
+  const int r = h->chi[k], mR = 4 * h->chi[k + 1], mL = 4 * h->chi[k - 1];
+  cplx<T>* Y = S_<T>(h, k);
+  cplx<T>* tmp = (cplx<T>*)h->tmp;
+  int rk = 0;
+  double* S = record ? h->dS + (k - 1) : nullptr;
+  double* sch = record ? h->dschmidt + (size_t)(k - 1) * h->chi_max : nullptr;
+  int rc = svd_select<T>(h, Y, r, mR, mR, r, false, S, sch, &rk);
+  if (rc) return rc;
+  CK(h, gather_rows<T>(h, Y, mR, mR, rk, 0, 0, 1, (cplx<T>*)h->spare, mR));        // Lambda^-1 X'
+  swap_spare(h, k);
+  CK(h, gather_rows<T>(h, (cplx<T>*)h->vecs, r, r, rk, 1, 0, 2, tmp, rk));          // U Lambda / ||kept||
+  CK(h, cgemm<T>(h->st, mL, rk, r, S_<T>(h, k - 1), r, 0, tmp, rk, 0, (cplx<T>*)h->spare, rk));
+  swap_spare(h, k - 1);
+  h->chi[k] = rk;
+  h->centre = k - 1;
+  if (record) {
+    h->schmidt_len[k - 1] = rk;
+    h->s_valid[k - 1] = 1;
+  }
+  return MPO_OK;
+}
+
+template <typename T>
+static int move_centre(mpo_ctx* h, int lo, int hi) {
+  while (h->centre < lo) { int rc = move_right<T>(h, h->centre); if (rc) return rc; }
+  while (h->centre > hi) { int rc = move_left<T>(h, h->centre, false); if (rc) return rc; }
+  return MPO_OK;
+}
+
+// One noisy gate on sites (i, i+1), superoperator M on the device.
+template <typename T>
+static int gate_update(mpo_ctx* h, int i, const cplx<T>* M) {
+  int rc = move_centre<T>(h, i, i + 1);
+  if (rc) return rc;
+  const int chiL = h->chi[i], chiM = h->chi[i + 1], chiR = h->chi[i + 2];
+  const int mL = 4 * chiL, mR = 4 * chiR;
+  cplx<T>* A0 = S_<T>(h, i);
+  cplx<T>* A1 = S_<T>(h, i + 1);
+  cplx<T>* th = (cplx<T>*)h->theta;
+  CK(h, cgemm<T>(h->st, mL, mR, chiM, A0, chiM, 0, A1, mR, 0, th, mR));        // theta
+  apply_superop_kernel<T><<<grid_for((size_t)chiL * chiR, h->num_sms), 256, 0, h->st>>>(th, chiL, chiR, M);
+  CK(h, cudaGetLastError());
+  int k = 0;
+  if (mL <= mR) {
+    // theta' = U X', rows of X' = Lambda W^H
+    rc = svd_select<T>(h, th, mL, mR, mR, h->chi_max, true, nullptr, nullptr, &k);
+    if (rc) return rc;
+    CK(h, gather_rows<T>(h, (cplx<T>*)h->vecs, mL, mL, k, 1, 0, 0, A0, k));     // U_k -> site i
+    CK(h, gather_rows<T>(h, th, mR, mR, k, 0, 0, 3, A1, mR));                    // Lambda W^H / ||kept||
+  } else {
+    // theta'^H = U X'  =>  theta' = X'^H U^H
+    cplx<T>* Y = (cplx<T>*)h->theta2;
+    CK(h, conj_transpose<T>(h, th, mL, mR, mR, Y, mL));
+    rc = svd_select<T>(h, Y, mR, mL, mL, h->chi_max, true, nullptr, nullptr, &k);
+    if (rc) return rc;
+    CK(h, gather_rows<T>(h, (cplx<T>*)h->vecs, mR, mR, k, 0, 1, 2, A1, mR));    // Lambda U^H / ||kept||
+    CK(h, gather_rows<T>(h, Y, mL, mL, k, 1, 1, 1, A0, k));                      // X'^H Lambda^-1
+  }
+  h->chi[i + 1] = k;
+  h->centre = i + 1;
+  return MPO_OK;
+}
+
+template <typename T>
+static int sweep_all(mpo_ctx* h) {
+  std::fill(h->s_valid.begin(), h->s_valid.end(), 0);
+  if (h->opts.smode == MPO_S_CENTRE) {
+    const int k = h->n / 2;
+    int rc = move_centre<T>(h, k, k);
+    if (rc) return rc;
+    return move_left<T>(h, k, true);
+  }
+  int rc = move_centre<T>(h, h->n - 1, h->n - 1);
+  if (rc) return rc;
+  for (int k = h->n - 1; k >= 1; --k) {
+    rc = move_left<T>(h, k, true);
+    if (rc) return rc;
+  }
+  return MPO_OK;
+}
+
+// ---------------------------------------------------------- gate staging ----
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Stage ng gates and rates on the device and build their superoperators into h->Ms.
+template <typename T>
+static int stage_gates(mpo_ctx* h, int ng, const double* gates, const double* p, int p_stride) {
+  const double2* dg = (const double2*)gates;
+  if (!is_device_ptr(gates)) {
+    CK(h, cudaMemcpyAsync(h->dgates, gates, sizeof(double2) * 16 * ng, cudaMemcpyHostToDevice, h->st));
+    dg = h->dgates;
+  }
+  const double* dp = p;
+  int stride = p_stride;
+  if (!is_device_ptr(p)) {
+    std::vector<double> hp(ng);
+    for (int i = 0; i < ng; ++i) {
+      hp[i] = p[(size_t)i * p_stride];
+      if (!(hp[i] >= 0.0 && hp[i] <= 1.0)) return fail(h, MPO_ERR_ARG, "p must lie in [0, 1]");
+    }
+    CK(h, cudaMemcpyAsync(h->dp, hp.data(), sizeof(double) * ng, cudaMemcpyHostToDevice, h->st));
+    CK(h, cudaStreamSynchronize(h->st));   // hp is a pageable temporary
+    dp = h->dp;
+    stride = 1;
+  }
+  build_superop_kernel<T><<<ng, 256, 0, h->st>>>(dg, dp, stride, (cplx<T>*)h->Ms);
+  CK(h, cudaGetLastError());
+  return MPO_OK;
+}
+
+template <typename T>
+static int apply_layer_t(mpo_ctx* h, int parity, const double* gates, const double* p, int p_stride) {
+  const int ng = (h->n - parity) / 2;   // parity 0: n/2 gates; parity 1: n/2 - 1
+  CK(h, cudaMemsetAsync(h->scal + 1, 0, sizeof(double), h->st));
+  if (ng > 0) {
+    int rc = stage_gates<T>(h, ng, gates, p, p_stride);
+    if (rc) return rc;
+    for (int g = 0; g < ng; ++g) {
+      rc = gate_update<T>(h, 2 * g + parity, (const cplx<T>*)h->Ms + (size_t)g * 256);
+      if (rc) return rc;
+    }
+  }
+  return sweep_all<T>(h);
+}
+
+template <typename T>
+static int trace_t(mpo_ctx* h, double* tr) {
+  double2 one = make_double2(1.0, 0.0);
+  CK(h, cudaMemcpyAsync(h->tv0, &one, sizeof(double2), cudaMemcpyHostToDevice, h->st));
+  double2 *a = h->tv0, *b = h->tv1;
+  for (int k = 0; k < h->n; ++k) {
+    const int cl = h->chi[k], cr = h->chi[k + 1];
+    trace_step_kernel<T><<<(cr + 127) / 128, 128, 0, h->st>>>(S_<T>(h, k), cl, cr, a, b);
+    CK(h, cudaGetLastError());
+    std::swap(a, b);
+  }
+  double2 v;
+  double ln;
+  CK(h, cudaMemcpyAsync(&v, a, sizeof(double2), cudaMemcpyDeviceToHost, h->st));
+  CK(h, cudaMemcpyAsync(&ln, h->scal, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(h, cudaStreamSynchronize(h->st));
+  *tr = v.x * std::exp(ln);
+  return MPO_OK;
+}
+
+// ================================================================ C ABI ====
+extern "C" {
+
+void mpo_default_opts(mpo_opts* o) {
+  if (!o) return;
+  o->eig_max_sweeps = 40;
+  o->sv_rel_cutoff = 0.0;
+  o->arena_cap_bytes = 0;
+  o->smode = MPO_S_ALL_BONDS;
+  o->barrier_timeout_s = 5.0;
+}
+
+const char* mpo_version(void) { return "gb300-mpo 0.1 (sm_103a)"; }
+
+static int init_fail(mpo_ctx* h, int code, const std::string& m) {
+  g_last_init_error = m;
+  if (h) mpo_free(h);
+  return code;
+}
+
+int mpo_init(mpo_handle* out, int n, int chi_max, mpo_precision prec, void* stream, const mpo_opts* opts) {
+  if (!out) { g_last_init_error = "out is NULL"; return MPO_ERR_ARG; }
+  *out = nullptr;
+  if (n < 2 || n % 2 || n > 4096) { g_last_init_error = "n_qubits must be even, 2..4096"; return MPO_ERR_ARG; }
+  if (chi_max < 1 || chi_max > 4096) { g_last_init_error = "chi_max must be 1..4096"; return MPO_ERR_ARG; }
+  if (prec != MPO_FP64 && prec != MPO_FP32) { g_last_init_error = "unknown precision"; return MPO_ERR_ARG; }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    g_last_init_error = "no CUDA device";
+    return MPO_ERR_CUDA;
+  }
+  mpo_ctx* h = new mpo_ctx();
+  h->n = n;
+  h->chi_max = chi_max;
+  h->prec = prec;
+  h->st = (cudaStream_t)stream;
+  mpo_default_opts(&h->opts);
+  if (opts) h->opts = *opts;
+  if (h->opts.eig_max_sweeps <= 0) h->opts.eig_max_sweeps = 40;
+  if (!(h->opts.barrier_timeout_s > 0.0)) h->opts.barrier_timeout_s = 5.0;
+  h->cutoff = h->opts.sv_rel_cutoff > 0.0 ? h->opts.sv_rel_cutoff : (prec == MPO_FP64 ? 1e-12 : 1e-6);
+  if (cudaGetDevice(&h->device) != cudaSuccess) return init_fail(h, MPO_ERR_CUDA, "cudaGetDevice failed");
+  cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+  int coop = 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
+  if (!coop) return init_fail(h, MPO_ERR_CUDA, "device lacks cooperative launch");
+
+  h->esz = prec == MPO_FP64 ? sizeof(double2) : sizeof(float2);
+  const size_t rsz = prec == MPO_FP64 ? sizeof(double) : sizeof(float);
+  h->cap.resize(n + 1);
+  for (int b = 0; b <= n; ++b) h->cap[b] = cap_of(b, n, chi_max);
+  h->chi.assign(n + 1, 1);
+  h->site_cap = 0;
+  for (int k = 0; k < n; ++k) h->site_cap = std::max(h->site_cap, (size_t)h->cap[k] * 4 * h->cap[k + 1]);
+  size_t th = 0;
+  int m = 1;
+  for (int i = 0; i + 1 < n; ++i) {
+    th = std::max(th, (size_t)16 * h->cap[i] * h->cap[i + 2]);
+    m = std::max(m, 4 * std::min(h->cap[i], h->cap[i + 2]));
+  }
+  for (int b = 0; b <= n; ++b) m = std::max(m, h->cap[b]);
+  h->theta_cap = th;
+  h->m_cap = m;
+  const int jac_limit = prec == MPO_FP64 ? 8192 : 16384;   // rotation table must fit shared memory
+  if (m > jac_limit) return init_fail(h, MPO_ERR_ARG, "bond dimension too large for the eigen-solver's shared-memory table");
+  h->tmp_cap = (size_t)m * chi_max;
+  const int ngmax = n / 2;
+  const size_t need = (size_t)(n + 1) * h->site_cap * h->esz + 2 * th * h->esz + (size_t)m * m * h->esz +
+                      h->tmp_cap * h->esz + (size_t)m * (rsz + sizeof(int) + sizeof(double)) +
+                      (size_t)ngmax * 256 * h->esz + (size_t)ngmax * (16 * sizeof(double2) + sizeof(double)) +
+                      (size_t)(n - 1) * (1 + chi_max) * sizeof(double) + 2 * (size_t)chi_max * sizeof(double2) + 4096;
+  if (h->opts.arena_cap_bytes > 0 && need > h->opts.arena_cap_bytes)
+    return init_fail(h, MPO_ERR_OOM, "device memory needed (" + std::to_string(need) + " B) exceeds arena_cap_bytes");
+  size_t freeb = 0, totb = 0;
+  if (cudaMemGetInfo(&freeb, &totb) == cudaSuccess && need > freeb)
+    return init_fail(h, MPO_ERR_OOM, "device memory needed (" + std::to_string(need) + " B) exceeds free memory");
+
+  auto alloc = [&](void** p, size_t bytes) -> bool {
+    if (cudaMalloc(p, std::max<size_t>(bytes, 256)) != cudaSuccess) { cudaGetLastError(); *p = nullptr; return false; }
+    h->bytes += bytes;
+    return true;
+  };
+  h->site.assign(n, nullptr);
+  bool ok = true;
+  for (int k = 0; k < n && ok; ++k) ok = alloc(&h->site[k], h->site_cap * h->esz);
+  ok = ok && alloc(&h->spare, h->site_cap * h->esz);
+  ok = ok && alloc(&h->theta, th * h->esz);
+  ok = ok && alloc(&h->theta2, th * h->esz);
+  ok = ok && alloc(&h->vecs, (size_t)m * m * h->esz);
+  ok = ok && alloc(&h->tmp, h->tmp_cap * h->esz);
+  ok = ok && alloc(&h->wv, (size_t)m * rsz);
+  ok = ok && alloc((void**)&h->perm, (size_t)m * sizeof(int));
+  ok = ok && alloc((void**)&h->lam2, (size_t)m * sizeof(double));
+  ok = ok && alloc(&h->Ms, (size_t)std::max(1, ngmax) * 256 * h->esz);
+  ok = ok && alloc((void**)&h->dgates, (size_t)std::max(1, ngmax) * 16 * sizeof(double2));
+  ok = ok && alloc((void**)&h->dp, (size_t)std::max(1, ngmax) * sizeof(double));
+  ok = ok && alloc((void**)&h->dsup, 256 * sizeof(double2));
+  ok = ok && alloc((void**)&h->info, sizeof(SelectInfo));
+  ok = ok && alloc((void**)&h->ctl, sizeof(GridCtl));
+  ok = ok && alloc((void**)&h->osctl, sizeof(OSCtl));
+  ok = ok && alloc((void**)&h->scal, 4 * sizeof(double));
+  ok = ok && alloc((void**)&h->dS, (size_t)(n - 1) * sizeof(double));
+  ok = ok && alloc((void**)&h->dschmidt, (size_t)(n - 1) * chi_max * sizeof(double));
+  ok = ok && alloc((void**)&h->tv0, (size_t)(chi_max + 1) * sizeof(double2));
+  ok = ok && alloc((void**)&h->tv1, (size_t)(chi_max + 1) * sizeof(double2));
+  if (!ok) return init_fail(h, MPO_ERR_OOM, "cudaMalloc failed");
+  if (cudaMallocHost((void**)&h->hs, sizeof(HostSync)) != cudaSuccess) {
+    cudaGetLastError();
+    h->hs = nullptr;
+    return init_fail(h, MPO_ERR_CUDA, "cudaMallocHost failed");
+  }
+  // product state |0..0><0..0|: every site 1 x 4 x 1 with A[0][0][0] = 1 (Sec. 4.1)
+  std::vector<unsigned char> one(h->esz, 0);
+  if (prec == MPO_FP64) { double v = 1.0; memcpy(one.data(), &v, sizeof v); }
+  else { float v = 1.0f; memcpy(one.data(), &v, sizeof v); }
+  for (int k = 0; k < n; ++k) {
+    if (cudaMemsetAsync(h->site[k], 0, 4 * h->esz, h->st) != cudaSuccess ||
+        cudaMemcpyAsync(h->site[k], one.data(), h->esz, cudaMemcpyHostToDevice, h->st) != cudaSuccess)
+      return init_fail(h, MPO_ERR_CUDA, "initial state upload failed");
+  }
+  if (cudaMemsetAsync(h->scal, 0, 4 * sizeof(double), h->st) != cudaSuccess ||
+      cudaMemsetAsync(h->dS, 0, (size_t)(n - 1) * sizeof(double), h->st) != cudaSuccess ||
+      cudaStreamSynchronize(h->st) != cudaSuccess)
+    return init_fail(h, MPO_ERR_CUDA, "initial state upload failed");
+  h->schmidt_len.assign(n - 1, 1);
+  h->s_valid.assign(n - 1, 0);
+  // the product state's Schmidt values are (1): S = 0 at every bond
+  std::vector<double> s1((size_t)(n - 1) * chi_max, 0.0);
+  for (int b = 0; b < n - 1; ++b) s1[(size_t)b * chi_max] = 1.0;
+  if (cudaMemcpy(h->dschmidt, s1.data(), s1.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+    return init_fail(h, MPO_ERR_CUDA, "initial state upload failed");
+  std::fill(h->s_valid.begin(), h->s_valid.end(), 1);
+  h->centre = 0;
+  *out = h;
+  return MPO_OK;
+}
+
+void mpo_free(mpo_handle h) {
+  if (!h) return;
+  for (void* p : h->site) if (p) cudaFree(p);
+  void* ps[] = {h->spare, h->theta, h->theta2, h->osctl, h->vecs, h->tmp, h->wv, h->perm, h->lam2, h->Ms, h->dgates,
+                h->dsup, h->dp, h->info, h->ctl, h->scal, h->dS, h->dschmidt, h->tv0, h->tv1};
+  for (void* p : ps) if (p) cudaFree(p);
+  if (h->hs) cudaFreeHost(h->hs);
+  delete h;
+}
+
+const char* mpo_last_error(mpo_handle h) {
+  if (!h) return g_last_init_error.c_str();
+  return h->msg.c_str();
+}
+
+#define GUARD(h)                                      \
+  do {                                                \
+    if (!(h)) return MPO_ERR_ARG;                     \
+    if ((h)->failed) return MPO_ERR_STATE;            \
+    cudaSetDevice((h)->device);                       \
+  } while (0)
+
+int mpo_apply_layer(mpo_handle h, int parity, const double* gates, const double* p, int p_stride) {
+  GUARD(h);
+  if (parity != 0 && parity != 1) return fail(h, MPO_ERR_ARG, "parity must be 0 or 1");
+  const int ng = (h->n - parity) / 2;
+  if (ng > 0 && (!gates || !p || p_stride < 0)) return fail(h, MPO_ERR_ARG, "gates/p must be non-NULL, p_stride >= 0");
+  return h->prec == MPO_FP64 ? apply_layer_t<double>(h, parity, gates, p, p_stride)
+                             : apply_layer_t<float>(h, parity, gates, p, p_stride);
+}
+
+int mpo_apply_gate(mpo_handle h, int bond, const double* gate, double p) {
+  GUARD(h);
+  if (bond < 0 || bond > h->n - 2 || !gate) return fail(h, MPO_ERR_ARG, "bad bond or gate");
+  if (h->prec == MPO_FP64) {
+    int rc = stage_gates<double>(h, 1, gate, &p, 0);
+    return rc ? rc : gate_update<double>(h, bond, (const double2*)h->Ms);
+  }
+  int rc = stage_gates<float>(h, 1, gate, &p, 0);
+  return rc ? rc : gate_update<float>(h, bond, (const float2*)h->Ms);
+}
+
+int mpo_apply_superop(mpo_handle h, int bond, const double* M) {
+  GUARD(h);
+  if (bond < 0 || bond > h->n - 2 || !M) return fail(h, MPO_ERR_ARG, "bad bond or superoperator");
+  const double2* src = (const double2*)M;
+  if (!is_device_ptr(M)) {
+    CK(h, cudaMemcpyAsync(h->dsup, M, sizeof(double2) * 256, cudaMemcpyHostToDevice, h->st));
+    src = h->dsup;
+  }
+  if (h->prec == MPO_FP64) cast_superop_kernel<double><<<1, 256, 0, h->st>>>(src, (double2*)h->Ms);
+  else cast_superop_kernel<float><<<1, 256, 0, h->st>>>(src, (float2*)h->Ms);
+  CK(h, cudaGetLastError());
+  return h->prec == MPO_FP64 ? gate_update<double>(h, bond, (const double2*)h->Ms)
+                             : gate_update<float>(h, bond, (const float2*)h->Ms);
+}
+
+int mpo_sweep(mpo_handle h) {
+  GUARD(h);
+  return h->prec == MPO_FP64 ? sweep_all<double>(h) : sweep_all<float>(h);
+}
+
+int mpo_entropy(mpo_handle h, double* S, double* trace, double* discarded) {
+  GUARD(h);
+  if (!S) return fail(h, MPO_ERR_ARG, "S is NULL");
+  std::vector<double> hS(h->n - 1);
+  double disc = 0.0;
+  CK(h, cudaMemcpyAsync(hS.data(), h->dS, sizeof(double) * (h->n - 1), cudaMemcpyDeviceToHost, h->st));
+  CK(h, cudaMemcpyAsync(&disc, h->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(h, cudaStreamSynchronize(h->st));
+  for (int b = 0; b < h->n - 1; ++b) S[b] = h->s_valid[b] ? hS[b] : NAN;
+  if (discarded) *discarded = disc;
+  if (trace) {
+    int rc = h->prec == MPO_FP64 ? trace_t<double>(h, trace) : trace_t<float>(h, trace);
+    if (rc) return rc;
+  }
+  return MPO_OK;
+}
+
+int mpo_schmidt(mpo_handle h, int bond, double* lam, int* len) {
+  GUARD(h);
+  if (bond < 0 || bond > h->n - 2 || !lam || !len) return fail(h, MPO_ERR_ARG, "bad bond or NULL output");
+  if (!h->s_valid[bond]) return fail(h, MPO_ERR_STATE, "no Schmidt values recorded for this bond");
+  const int L = h->schmidt_len[bond];
+  std::vector<double> p(L);
+  CK(h, cudaMemcpyAsync(p.data(), h->dschmidt + (size_t)bond * h->chi_max, sizeof(double) * L,
+                        cudaMemcpyDeviceToHost, h->st));
+  CK(h, cudaStreamSynchronize(h->st));
+  for (int i = 0; i < L; ++i) lam[i] = std::sqrt(std::max(0.0, p[i]));
+  *len = L;
+  return MPO_OK;
+}
+
+int mpo_bond_dims(mpo_handle h, int* dims) {
+  GUARD(h);
+  if (!dims) return fail(h, MPO_ERR_ARG, "dims is NULL");
+  for (int b = 0; b <= h->n; ++b) dims[b] = h->chi[b];
+  return MPO_OK;
+}
+
+int mpo_centre(mpo_handle h, int* c) {
+  GUARD(h);
+  if (!c) return fail(h, MPO_ERR_ARG, "NULL");
+  *c = h->centre;
+  return MPO_OK;
+}
+
+size_t mpo_device_bytes(mpo_handle h) { return h ? h->bytes : 0; }
+
+int mpo_get_site(mpo_handle h, int k, double* buf, int* chiL, int* chiR) {
+  GUARD(h);
+  if (k < 0 || k >= h->n || !chiL || !chiR) return fail(h, MPO_ERR_ARG, "bad site index");
+  *chiL = h->chi[k];
+  *chiR = h->chi[k + 1];
+  if (!buf) return MPO_OK;
+  const size_t cnt = (size_t)h->chi[k] * 4 * h->chi[k + 1];
+  double ln = 0.0;
+  CK(h, cudaMemcpyAsync(&ln, h->scal, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  if (h->prec == MPO_FP64) {
+    CK(h, cudaMemcpyAsync(buf, h->site[k], cnt * sizeof(double2), cudaMemcpyDeviceToHost, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+  } else {
+    std::vector<float> f(2 * cnt);
+    CK(h, cudaMemcpyAsync(f.data(), h->site[k], cnt * sizeof(float2), cudaMemcpyDeviceToHost, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+    for (size_t i = 0; i < 2 * cnt; ++i) buf[i] = f[i];
+  }
+  if (k == h->centre) {
+    const double s = std::exp(ln);
+    for (size_t i = 0; i < 2 * cnt; ++i) buf[i] *= s;
+  }
+  return MPO_OK;
+}
+
+int mpo_to_dense(mpo_handle h, double* rho_vec) {
+  GUARD(h);
+  if (!rho_vec || h->n > 12) return fail(h, MPO_ERR_ARG, "to_dense needs n <= 12 and a buffer");
+  // T: rows = 4^j combined physical index, cols = current bond
+  std::vector<double> T(2, 0.0);
+  T[0] = 1.0;
+  size_t rows = 1;
+  int bond = 1;
+  for (int k = 0; k < h->n; ++k) {
+    int cl, cr;
+    mpo_get_site(h, k, nullptr, &cl, &cr);
+    std::vector<double> A((size_t)cl * 4 * cr * 2);
+    int rc = mpo_get_site(h, k, A.data(), &cl, &cr);
+    if (rc) return rc;
+    if (cl != bond) return fail(h, MPO_ERR_STATE, "inconsistent bond dimensions");
+    std::vector<double> Tn(rows * 4 * cr * 2, 0.0);
+    for (size_t r = 0; r < rows; ++r)
+      for (int a = 0; a < cl; ++a) {
+        const double tr = T[(r * cl + a) * 2], ti = T[(r * cl + a) * 2 + 1];
+        if (tr == 0.0 && ti == 0.0) continue;
+        for (int I = 0; I < 4; ++I)
+          for (int c = 0; c < cr; ++c) {
+            const double ar = A[(((size_t)a * 4 + I) * cr + c) * 2], ai = A[(((size_t)a * 4 + I) * cr + c) * 2 + 1];
+            const size_t o = ((r * 4 + I) * cr + c) * 2;
+            Tn[o] += tr * ar - ti * ai;
+            Tn[o + 1] += tr * ai + ti * ar;
+          }
+      }
+    T.swap(Tn);
+    rows *= 4;
+    bond = cr;
+  }
+  memcpy(rho_vec, T.data(), rows * 2 * sizeof(double));
+  return MPO_OK;
+}
+
+int mpo_svd(int r, int c, void* X, void* w, void* Ut, mpo_precision prec, int max_sweeps, void* stream) {
+  if (r < 1 || c < 1 || !X || !w || !Ut) return MPO_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MPO_ERR_CUDA;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  OSCtl* ctl = nullptr;
+  if (cudaMalloc(&ctl, sizeof(OSCtl)) != cudaSuccess) return MPO_ERR_OOM;
+  const int ms = max_sweeps > 0 ? max_sweeps : 40;
+  cudaError_t e = prec == MPO_FP64
+      ? launch_onesided<double>(st, (double2*)X, r, c, c, (double2*)Ut, (double*)w, ctl, ms, 5.0, sms)
+      : launch_onesided<float>(st, (float2*)X, r, c, c, (float2*)Ut, (float*)w, ctl, ms, 5.0, sms);
+  GridCtl hc{};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, &ctl->g, sizeof(GridCtl), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(ctl);
+  if (e != cudaSuccess) { g_last_init_error = cudaGetErrorString(e); return MPO_ERR_CUDA; }
+  if (hc.err) return MPO_ERR_TIMEOUT;
+  if (hc.status) return MPO_ERR_NOCONV;
+  return MPO_OK;
+}
+
+int mpo_eigh(int m, void* A, void* w, void* V, mpo_precision prec, int max_sweeps, void* stream) {
+  if (m < 1 || !A || !w || !V) return MPO_ERR_ARG;
+  const int lim = prec == MPO_FP64 ? 8192 : 16384;
+  if (m > lim) return MPO_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MPO_ERR_CUDA;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  GridCtl* ctl = nullptr;
+  if (cudaMalloc(&ctl, sizeof(GridCtl)) != cudaSuccess) return MPO_ERR_OOM;
+  cudaError_t e = prec == MPO_FP64
+      ? launch_jacobi<double>(st, (double2*)A, m, (double2*)V, (double*)w, ctl, max_sweeps > 0 ? max_sweeps : 40, 5.0, sms)
+      : launch_jacobi<float>(st, (float2*)A, m, (float2*)V, (float*)w, ctl, max_sweeps > 0 ? max_sweeps : 40, 5.0, sms);
+  GridCtl hc{};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, ctl, sizeof(GridCtl), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(ctl);
+  if (e != cudaSuccess) { g_last_init_error = cudaGetErrorString(e); return MPO_ERR_CUDA; }
+  if (hc.err) return MPO_ERR_TIMEOUT;
+  if (hc.status) return MPO_ERR_NOCONV;
+  return MPO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,246 @@
+"""Python binding of the C ABI in include/mpo.h (argument marshalling only).
+
+Every step of the simulation runs in the CUDA library; this module converts
+arrays and handles. There is no CPU fallback: if the library is missing or no
+GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MPO_FP64, MPO_FP32 = 0, 1
+MPO_S_ALL_BONDS, MPO_S_CENTRE = 0, 1
+ERRORS = {0: "MPO_OK", -1: "MPO_ERR_ARG", -2: "MPO_ERR_CUDA", -3: "MPO_ERR_OOM", -4: "MPO_ERR_NOCONV",
+          -5: "MPO_ERR_TIMEOUT", -6: "MPO_ERR_STATE"}
+EXPORTS = ["mpo_default_opts", "mpo_init", "mpo_apply_layer", "mpo_apply_gate", "mpo_apply_superop", "mpo_sweep",
+           "mpo_entropy", "mpo_schmidt", "mpo_bond_dims", "mpo_get_site", "mpo_to_dense", "mpo_centre",
+           "mpo_device_bytes", "mpo_free", "mpo_last_error", "mpo_eigh", "mpo_svd", "mpo_version"]
+
+
+class MPOError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("eig_max_sweeps", ctypes.c_int), ("sv_rel_cutoff", ctypes.c_double),
+                ("arena_cap_bytes", ctypes.c_size_t), ("smode", ctypes.c_int),
+                ("barrier_timeout_s", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load the built library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built ({path}); run paper_2003_13163_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P, I, D, Z = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    IP, DP = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "mpo_default_opts": (None, [ctypes.POINTER(Opts)]),
+        "mpo_init": (I, [ctypes.POINTER(P), I, I, I, P, ctypes.POINTER(Opts)]),
+        "mpo_apply_layer": (I, [P, I, P, P, I]),
+        "mpo_apply_gate": (I, [P, I, P, D]),
+        "mpo_apply_superop": (I, [P, I, P]),
+        "mpo_sweep": (I, [P]),
+        "mpo_entropy": (I, [P, DP, DP, DP]),
+        "mpo_schmidt": (I, [P, I, DP, IP]),
+        "mpo_bond_dims": (I, [P, IP]),
+        "mpo_get_site": (I, [P, I, P, IP, IP]),
+        "mpo_to_dense": (I, [P, P]),
+        "mpo_centre": (I, [P, IP]),
+        "mpo_device_bytes": (Z, [P]),
+        "mpo_free": (None, [P]),
+        "mpo_last_error": (ctypes.c_char_p, [P]),
+        "mpo_eigh": (I, [I, P, P, P, I, I, P]),
+        "mpo_svd": (I, [I, I, P, P, P, I, I, P]),
+        "mpo_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a) -> int:
+    """Raw address of a numpy array or a torch tensor (host or device)."""
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return ctypes.c_void_p(0)
+
+
+def default_opts() -> Opts:
+    o = Opts()
+    load_library().mpo_default_opts(ctypes.byref(o))
+    return o
+
+
+class MPO:
+    """Handle on one device-resident MPO (see include/mpo.h)."""
+
+    def __init__(self, n: int, chi_max: int, precision: str = "fp64", *, cutoff: float = 0.0,
+                 eig_max_sweeps: int = 0, arena_cap_bytes: int = 0, centre_only: bool = False,
+                 barrier_timeout_s: float = 0.0, stream=None):
+        lib = load_library()
+        self._lib = lib
+        self.n, self.chi_max = n, chi_max
+        self.prec = {"fp64": MPO_FP64, "fp32": MPO_FP32}[precision]
+        o = default_opts()
+        if cutoff > 0:
+            o.sv_rel_cutoff = cutoff
+        if eig_max_sweeps > 0:
+            o.eig_max_sweeps = eig_max_sweeps
+        o.arena_cap_bytes = arena_cap_bytes
+        o.smode = MPO_S_CENTRE if centre_only else MPO_S_ALL_BONDS
+        if barrier_timeout_s > 0:
+            o.barrier_timeout_s = barrier_timeout_s
+        h = ctypes.c_void_p()
+        st = ctypes.c_void_p(stream) if stream is not None else _current_stream()
+        rc = lib.mpo_init(ctypes.byref(h), n, chi_max, self.prec, st, ctypes.byref(o))
+        if rc != 0:
+            raise MPOError(rc, lib.mpo_last_error(None).decode())
+        self.h = h
+
+    def _check(self, rc):
+        if rc != 0:
+            raise MPOError(rc, self._lib.mpo_last_error(self.h).decode())
+
+    def apply_layer(self, parity: int, gates, p) -> None:
+        """gates: (n_gates, 4, 4) complex128 (numpy, or a CUDA tensor viewed as
+        float64 pairs); p: scalar or (n_gates,) float64."""
+        if isinstance(gates, np.ndarray):
+            gates = np.ascontiguousarray(gates, dtype=np.complex128)
+        if np.isscalar(p):
+            pa, stride = np.array([float(p)]), 0
+        elif isinstance(p, np.ndarray):
+            pa, stride = np.ascontiguousarray(p, dtype=np.float64), 1
+        else:
+            pa, stride = p, 1
+        self._check(self._lib.mpo_apply_layer(self.h, parity, _ptr(gates), _ptr(pa), stride))
+
+    def apply_gate(self, bond: int, U: np.ndarray, p: float) -> None:
+        U = np.ascontiguousarray(U, dtype=np.complex128)
+        self._check(self._lib.mpo_apply_gate(self.h, bond, _ptr(U), float(p)))
+
+    def apply_superop(self, bond: int, M: np.ndarray) -> None:
+        M = np.ascontiguousarray(M, dtype=np.complex128)
+        self._check(self._lib.mpo_apply_superop(self.h, bond, _ptr(M)))
+
+    def sweep(self) -> None:
+        self._check(self._lib.mpo_sweep(self.h))
+
+    def entropy(self, with_trace: bool = True):
+        S = np.empty(self.n - 1)
+        tr, dw = ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.mpo_entropy(self.h, S.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                          ctypes.byref(tr) if with_trace else None, ctypes.byref(dw)))
+        return S, (tr.value if with_trace else None), dw.value
+
+    def schmidt(self, bond: int) -> np.ndarray:
+        lam = np.empty(self.chi_max)
+        ln = ctypes.c_int()
+        self._check(self._lib.mpo_schmidt(self.h, bond, lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                          ctypes.byref(ln)))
+        return lam[: ln.value].copy()
+
+    def bond_dims(self) -> np.ndarray:
+        d = np.empty(self.n + 1, dtype=np.int32)
+        self._check(self._lib.mpo_bond_dims(self.h, d.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+        return d
+
+    def site(self, k: int) -> np.ndarray:
+        cl, cr = ctypes.c_int(), ctypes.c_int()
+        self._check(self._lib.mpo_get_site(self.h, k, None, ctypes.byref(cl), ctypes.byref(cr)))
+        buf = np.empty((cl.value, 4, cr.value), dtype=np.complex128)
+        self._check(self._lib.mpo_get_site(self.h, k, _ptr(buf), ctypes.byref(cl), ctypes.byref(cr)))
+        return buf
+
+    def to_dense(self) -> np.ndarray:
+        out = np.empty((4,) * self.n, dtype=np.complex128)
+        self._check(self._lib.mpo_to_dense(self.h, _ptr(out)))
+        return out
+
+    def centre(self) -> int:
+        c = ctypes.c_int()
+        self._check(self._lib.mpo_centre(self.h, ctypes.byref(c)))
+        return c.value
+
+    def device_bytes(self) -> int:
+        return int(self._lib.mpo_device_bytes(self.h))
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self._lib.mpo_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def eigh(A, precision: str = "fp64", max_sweeps: int = 0):
+    """Hermitian eigen-solve on the device through the C ABI (test export).
+
+    A: CUDA torch tensor (m, m) complex128/complex64, overwritten. Returns
+    (w, V) torch tensors (unsorted)."""
+    import torch
+    lib = load_library()
+    m = A.shape[0]
+    prec = {"fp64": MPO_FP64, "fp32": MPO_FP32}[precision]
+    rdt = torch.float64 if prec == MPO_FP64 else torch.float32
+    w = torch.empty(m, dtype=rdt, device=A.device)
+    V = torch.empty_like(A)
+    rc = lib.mpo_eigh(m, A.data_ptr(), w.data_ptr(), V.data_ptr(), prec, max_sweeps,
+                      ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if rc != 0:
+        raise MPOError(rc, "mpo_eigh failed")
+    return w, V
+
+
+def svd_rows(X, precision: str = "fp64", max_sweeps: int = 0):
+    """One-sided Jacobi SVD on the device (test export). X: CUDA tensor (r, c),
+    overwritten with U^H X. Returns (w, Ut): squared row norms and U^T."""
+    import torch
+    lib = load_library()
+    r, c = X.shape
+    prec = {"fp64": MPO_FP64, "fp32": MPO_FP32}[precision]
+    rdt = torch.float64 if prec == MPO_FP64 else torch.float32
+    w = torch.empty(r, dtype=rdt, device=X.device)
+    Ut = torch.empty((r, r), dtype=X.dtype, device=X.device)
+    rc = lib.mpo_svd(r, c, X.data_ptr(), w.data_ptr(), Ut.data_ptr(), prec, max_sweeps,
+                     ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if rc != 0:
+        raise MPOError(rc, "mpo_svd failed")
+    return w, Ut

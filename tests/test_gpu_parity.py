@@ -1,0 +1,257 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances: the plain FP64 form must match the oracle to 1e-10 in every MPO
+entropy (the FP64 target); the FP32 form is checked against a bound derived
+from FP32 rounding of the Gram matrices (Schmidt values resolved to about
+sqrt(eps_32) of the largest), stated per test.
+"""
+import numpy as np
+import pytest
+
+from oracle import channels, dense, mpo as ompo, statevec
+from paper_2003_13163_gb300.circuits import random_circuit, random_hermitian_psd, random_complex
+from tests.gpu_util import need_gpu, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    return need_gpu()
+
+
+# ------------------------------------------------------------ eigen-solver --
+@pytest.mark.parametrize("m,decay", [(1, 0.0), (5, 0.3), (64, 0.2), (257, 0.05), (600, 0.02)])
+def test_eigh_fp64_matches_lapack(M, m, decay):
+    import torch
+    A = random_hermitian_psd(m, decay, seed=m)
+    if m > 1:
+        A = A + 1e-3 * (lambda z: z + z.conj().T)(random_complex((m, m), seed=m + 1))
+    At = torch.tensor(A, device="cuda")
+    w, V = M.eigh(At.clone(), "fp64")
+    w, V = w.cpu().numpy(), V.cpu().numpy()
+    ref = np.linalg.eigvalsh(A)
+    scale = np.abs(ref).max()
+    np.testing.assert_allclose(np.sort(w), ref, atol=1e-12 * scale * max(1, np.sqrt(m)))
+    np.testing.assert_allclose(V.conj().T @ V, np.eye(m), atol=1e-12 * max(1, m))
+    np.testing.assert_allclose((V * w[None, :]) @ V.conj().T, A, atol=1e-12 * scale * max(1, m))
+
+
+@pytest.mark.parametrize("m", [33, 300])
+def test_eigh_fp32(M, m):
+    import torch
+    A = random_hermitian_psd(m, 0.05, seed=3 * m)
+    w, V = M.eigh(torch.tensor(A.astype(np.complex64), device="cuda"), "fp32")
+    w, V = w.cpu().numpy().astype(np.float64), V.cpu().numpy().astype(np.complex128)
+    np.testing.assert_allclose(np.sort(w), np.linalg.eigvalsh(A), atol=2e-5 * np.sqrt(m))
+    np.testing.assert_allclose(V.conj().T @ V, np.eye(m), atol=2e-5 * np.sqrt(m))
+
+
+@pytest.mark.parametrize("r,c,decay", [(1, 7, 0.0), (6, 6, 0.5), (64, 256, 0.3), (300, 300, 0.08), (517, 1024, 0.03)])
+def test_onesided_svd_fp64_matches_lapack(M, r, c, decay):
+    """Singular values with exponentially decaying spectrum (Fig. 7 shape) down
+    to ~1e-13 of the largest keep their relative accuracy."""
+    import torch
+    k = min(r, c)
+    U = np.linalg.qr(random_complex((r, k), seed=r))[0]
+    Vh = np.linalg.qr(random_complex((c, k), seed=c + 1))[0].conj().T
+    s = np.exp(-decay * np.arange(k))
+    X = (U * s[None, :]) @ Vh
+    Xt = torch.tensor(X, device="cuda")
+    w, Ut = M.svd_rows(Xt, "fp64")
+    w, Ut, Xo = w.cpu().numpy(), Ut.cpu().numpy(), Xt.cpu().numpy()
+    sv = np.sqrt(np.sort(np.maximum(w, 0))[::-1])[:k]
+    ref = np.linalg.svd(X, compute_uv=False)
+    big = ref > 1e-13 * ref[0]
+    np.testing.assert_allclose(sv[big], ref[big], rtol=1e-9, atol=1e-15 * ref[0])
+    Um = Ut.T
+    np.testing.assert_allclose(Um.conj().T @ Um, np.eye(r), atol=1e-13 * np.sqrt(r))
+    np.testing.assert_allclose(Um @ Xo, X, atol=1e-13 * ref[0] * np.sqrt(c))
+    G = Xo @ Xo.conj().T
+    off = G - np.diag(np.diag(G))
+    assert np.abs(off).max() < 1e-13 * ref[0] ** 2 * np.sqrt(c)
+
+
+def test_eigh_iteration_cap_reports_noconv(M):
+    import torch
+    A = random_hermitian_psd(64, 0.1, seed=9)
+    with pytest.raises(M.MPOError) as e:
+        M.eigh(torch.tensor(A, device="cuda"), "fp64", max_sweeps=1)
+    assert e.value.code == -4
+
+
+# --------------------------------------------------------------- states -----
+def test_initial_product_state(M):
+    m = M.MPO(8, 16)
+    S, tr, dw = m.entropy()
+    assert np.all(S == 0.0) and abs(tr - 1.0) < 1e-15 and dw == 0.0
+    T = m.to_dense()
+    np.testing.assert_allclose(T, dense.initial_vec(8), atol=0)
+
+
+def test_single_gate_dense_state(M):
+    c = random_circuit(4, 1, 0.05, seed=21)
+    m = M.MPO(4, 16)
+    m.apply_gate(1, c.gates[0][0], 0.05)
+    T = dense.apply_superop(dense.initial_vec(4), channels.noisy_gate_superop(c.gates[0][0], 0.05), 2)
+    np.testing.assert_allclose(m.to_dense(), T, atol=1e-13)
+
+
+def test_superop_builder_matches_oracle(M):
+    """The device superoperator (closed form of Sec. 2.2) equals the oracle's
+    (Pauli-sum form): check through a product-state gate on n = 2."""
+    U = random_circuit(2, 1, 0.0, seed=5).gates[0][0]
+    for p in (0.0, 0.013, 0.4, 15 / 16, 1.0):
+        m = M.MPO(2, 16)
+        m.apply_gate(0, U, p)
+        T = dense.apply_superop(dense.initial_vec(2), channels.noisy_gate_superop(U, p), 1)
+        np.testing.assert_allclose(m.to_dense(), T, atol=1e-14)
+
+
+# ------------------------------------------------------------- circuits -----
+def test_config_n8_exact_vs_dense_oracle(M):
+    """n = 8, depth 16, p = 0.02, chi_max = 256 (exact): S_l at every bond after
+    every step, Tr rho and the final |rho>> against the dense oracle, FP64."""
+    c = random_circuit(8, 16, 0.02, seed=0)
+    d = dense.run(c, 256)
+    S, tr, dw, m = run_gpu(M, c, 256)
+    assert np.abs(S - d.S).max() < 1e-10
+    np.testing.assert_allclose(tr, d.trace, atol=1e-12)
+    np.testing.assert_allclose(m.to_dense(), d.final, atol=1e-11)
+    assert dw.max() < 1e-12
+
+
+@pytest.mark.parametrize("n,chi,p,seed", [(8, 4, 0.05, 1), (8, 16, 0.02, 2), (10, 16, 0.05, 3), (10, 64, 0.01, 4)])
+def test_truncated_vs_oracles(M, n, chi, p, seed):
+    c = random_circuit(n, 8, p, seed=seed)
+    d = dense.run(c, chi, 1e-7)
+    o = ompo.run(c, chi, 1e-7, keep_schmidt=True)
+    S, tr, dw, m = run_gpu(M, c, chi, cutoff=1e-7)
+    assert np.abs(o.S - d.S).max() < 1e-9
+    assert np.abs(S - o.S).max() < 1e-9
+    np.testing.assert_allclose(tr, o.trace, atol=1e-10)
+    np.testing.assert_allclose(dw, [w.sum() for w in o.discarded], atol=1e-10)
+    assert dw.sum() > 0.0                       # the case truncates
+    for b in range(n - 1):                      # normalised Schmidt spectra of the last step
+        lam = m.schmidt(b)
+        ref = o.schmidt[-1][b]
+        ref = ref / np.sqrt((ref ** 2).sum())
+        L = min(len(lam), len(ref))
+        np.testing.assert_allclose(lam[:L], ref[:L], atol=1e-9)
+    assert list(m.bond_dims()[1:-1]) == o.bond_dims[-1]
+
+
+def test_noiseless_doubling(M):
+    c = random_circuit(10, 8, 0.0, seed=6)
+    S, tr, dw, _ = run_gpu(M, c, 1024)
+    np.testing.assert_allclose(S, 2 * statevec.run(c), atol=1e-9)
+    np.testing.assert_allclose(tr, 1.0, atol=1e-12)
+
+
+def test_full_depolarisation(M):
+    c = random_circuit(12, 2, 15 / 16, seed=7)
+    S, tr, dw, m = run_gpu(M, c, 64)
+    assert np.abs(S).max() < 1e-12
+    np.testing.assert_allclose(tr, 1.0, atol=1e-12)
+    assert list(m.bond_dims()) == [1] * 13
+
+
+def test_ghz_and_classical_pair(M):
+    n = 6
+    H = np.array([[1, 1], [1, -1]]) / np.sqrt(2)
+    CNOT = np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 0, 1], [0, 0, 1, 0]], dtype=complex)
+    m = M.MPO(n, 64)
+    for b in range(n - 1):
+        U = CNOT @ np.kron(H, np.eye(2)) if b == 0 else CNOT
+        m.apply_gate(b, U, 0.0)
+    m.sweep()
+    S, tr, _ = m.entropy()
+    np.testing.assert_allclose(S, 2.0, atol=1e-12)
+    Z1 = np.kron(np.diag([1.0, -1.0]), np.eye(2))
+    U = CNOT @ np.kron(H, np.eye(2))
+    Mop = channels.superop(lambda r: 0.5 * (U @ r @ U.conj().T) + 0.5 * Z1 @ (U @ r @ U.conj().T) @ Z1)
+    m2 = M.MPO(2, 16)
+    m2.apply_superop(0, Mop)
+    m2.sweep()
+    S2, tr2, _ = m2.entropy()
+    assert abs(S2[0] - 1.0) < 1e-12 and abs(tr2 - 1.0) < 1e-12
+
+
+def test_small_chains_and_empty_layers(M):
+    for n in (2, 4):
+        c = random_circuit(n, 5, 0.03, seed=n)
+        d = dense.run(c, 64)
+        S, tr, _, _ = run_gpu(M, c, 64)
+        assert np.abs(S - d.S).max() < 1e-11
+        np.testing.assert_allclose(tr, d.trace, atol=1e-12)
+
+
+def test_n32_truncated_vs_mpo_oracle(M):
+    """A longer chain deep in the truncated regime (n = 32, chi = 64, p = 0.01)."""
+    c = random_circuit(32, 10, 0.01, seed=1)
+    o = ompo.run(c, 64, 1e-7)
+    S, tr, dw, _ = run_gpu(M, c, 64, cutoff=1e-7)
+    assert np.abs(S - o.S).max() < 1e-9
+    np.testing.assert_allclose(tr, o.trace, rtol=1e-9)
+
+
+def test_centre_only_mode(M):
+    c = random_circuit(10, 6, 0.02, seed=8)
+    o = ompo.run(c, 32, 1e-7)
+    S, tr, dw, _ = run_gpu(M, c, 32, cutoff=1e-7, centre_only=True)
+    np.testing.assert_allclose(S[:, 4], o.S[:, 4], atol=1e-9)
+    assert np.isnan(S[:, 0]).all()
+
+
+def test_fp32_form_error_bound(M):
+    """FP32 form on the n = 8 exact configuration: |dS| against the FP64 oracle
+    stays within the FP32 bound (Gram rounding ~ eps_32 * lambda_max^2)."""
+    c = random_circuit(8, 8, 0.02, seed=0)
+    d = dense.run(c, 256)
+    S, tr, _, _ = run_gpu(M, c, 256, precision="fp32")
+    err = np.abs(S - d.S).max()
+    print("fp32 max |dS| =", err)
+    assert err < 5e-3
+    np.testing.assert_allclose(tr, d.trace, atol=1e-4)
+
+
+# ---------------------------------------------------------- error paths -----
+def test_noconv_then_state_error(M):
+    c = random_circuit(8, 4, 0.02, seed=0)
+    m = M.MPO(8, 256, eig_max_sweeps=1)
+    with pytest.raises(M.MPOError) as e:
+        for t in range(1, 5):
+            m.apply_layer(c.parity(t), c.gates[t - 1], c.p[t - 1])
+    assert e.value.code == -4
+    with pytest.raises(M.MPOError) as e2:
+        m.entropy()
+    assert e2.value.code == -6
+
+
+def test_arena_cap_reports_oom(M):
+    with pytest.raises(M.MPOError) as e:
+        M.MPO(64, 1024, arena_cap_bytes=1 << 20)
+    assert e.value.code == -3
+
+
+def test_barrier_wait_limit_reports_timeout(M):
+    """A wait limit far below one round forces the grid barrier to give up:
+    the kernel returns early with a status, no fault, and the handle reports
+    MPO_ERR_TIMEOUT."""
+    c = random_circuit(10, 6, 0.02, seed=0)
+    m = M.MPO(10, 256, barrier_timeout_s=1e-9)
+    with pytest.raises(M.MPOError) as e:
+        for t in range(1, 7):
+            m.apply_layer(c.parity(t), c.gates[t - 1], c.p[t - 1])
+    assert e.value.code == -5
+    # the context stays usable
+    m2 = M.MPO(4, 16)
+    m2.apply_layer(0, c.gates[0][:2], 0.01)
+    assert np.isfinite(m2.entropy()[0]).all()
+
+
+def test_bad_arguments(M):
+    m = M.MPO(8, 16)
+    with pytest.raises(M.MPOError) as e:
+        m._check(m._lib.mpo_apply_gate(m.h, 9, None, 0.0))
+    assert e.value.code == -1
