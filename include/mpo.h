@@ -75,6 +75,12 @@ typedef struct {
   size_t arena_cap_bytes;   /* refuse device allocations above this total [0 = no cap] */
   mpo_entropy_mode smode;   /* [MPO_S_ALL_BONDS] */
   double barrier_timeout_s; /* limit of each device-side grid-barrier wait [5.0] */
+  int block_jacobi_min_rows;/* factorisations with at least this many rows use the block
+                               one-sided Jacobi SVD (pairs of 16-row blocks) instead of the
+                               row-pair one [0 = default: 64 for FP32, never for FP64;
+                               < 0 = never]. The block form needs far fewer passes over
+                               the matrix but resolves singular values only to about
+                               sqrt(eps) * sigma_max relative accuracy per row pair. */
 } mpo_opts;
 
 /* Fill *o with the defaults. */
@@ -153,6 +159,29 @@ int mpo_centre(mpo_handle h, int *centre);
 /* Device bytes held by the handle. */
 size_t mpo_device_bytes(mpo_handle h);
 
+/* Kernel timing. enable = 1 clears the counters and starts recording a CUDA
+ * event pair on the handle's stream around every kernel launch of the path;
+ * enable = 0 stops. Adds a little launch overhead while on; the paper has no
+ * counterpart (it is a measurement aid). */
+int mpo_profile(mpo_handle h, int enable);
+
+/* Totals for kernel class cls (0 .. 6: svd_jacobi, cgemm, superop, select,
+ * gather, transpose, trace) since the last mpo_profile(h, 1): summed event
+ * durations in ms, launch count, and the algorithmic flops and bytes of those
+ * launches as the library counts them (an SVD of an r x c matrix counts the
+ * Gram-plus-dense-eigensolver work 4 min^2 max + 13.3 min^3, a complex GEMM
+ * 8 M N K). Returns MPO_ERR_ARG past the last class. Synchronises the stream. */
+int mpo_profile_read(mpo_handle h, int cls, const char **name, double *ms, long long *launches, double *flops,
+                     double *bytes);
+
+/* Jacobi sweeps summed over the SVD launches recorded since mpo_profile(h, 1). */
+long long mpo_profile_sweeps(mpo_handle h);
+
+/* Wall time (ms) spent by the block Jacobi SVD in its three phases (Gram
+ * partials, pair eigen-solves, rotation apply; grid-barrier waits included),
+ * summed since mpo_profile(h, 1). ms3: host [3]. */
+int mpo_profile_phases(mpo_handle h, double *ms3);
+
 /* Release everything; NULL is a no-op. */
 void mpo_free(mpo_handle h);
 
@@ -169,14 +198,16 @@ const char *mpo_last_error(mpo_handle h);
 int mpo_eigh(int m, void *A, void *w, void *V, mpo_precision prec, int max_sweeps, void *cuda_stream);
 
 /* Stand-alone one-sided Jacobi SVD used by every factorisation of the path
- * (App. A's SVD of B, and the centre moves), exported for tests: X is r x c
+ * (App. A's SVD of B, and the centre moves), exported for tests. block = 0
+ * selects the row-pair (Hestenes) form, block = 1 the 16-row block form. X is r x c
  * complex (interleaved, row-major, leading dimension c), device pointer,
  * overwritten with U^H X, whose rows are mutually orthogonal. On return w
  * (device, [r]) holds the squared row norms (the squared singular values of
  * the input, unsorted) and Ut (device, r x r row-major) the transpose of the
  * unitary U, so input = U * output. Returns MPO_ERR_NOCONV when max_sweeps
  * (<= 64) is reached. */
-int mpo_svd(int r, int c, void *X, void *w, void *Ut, mpo_precision prec, int max_sweeps, void *cuda_stream);
+int mpo_svd(int r, int c, void *X, void *w, void *Ut, mpo_precision prec, int max_sweeps, int block,
+            void *cuda_stream);
 
 /* Library version string. */
 const char *mpo_version(void);

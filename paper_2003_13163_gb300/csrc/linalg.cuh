@@ -420,6 +420,7 @@ struct OSCtl {
   int active[64];   // rotations per sweep (grid-wide atomic counts)
   double scale;
   double pad;
+  unsigned long long phase_ns[4];   // CTA 0: wall time per phase (G, E, A), barrier waits included
 };
 
 template <typename T>
@@ -484,16 +485,19 @@ __global__ void __launch_bounds__(256) onesided_jacobi_kernel(cplx<T>* X, int r,
           gi = fma(x.y, y.x, fma(-x.x, y.y, gi));
         }
         warp_sum3<T>(a, b, gr, gi);
-        const T ag = hypot(gr, gi);
-        const T thr = fmax(tol_rel * sqrt(a * b), floor_abs);
-        if (!(ag > thr) || ag == T(0)) continue;
-        const T zeta = (b - a) / (T(2) * ag);
-        T t;
-        if (fabs(zeta) > T(1) / eps_of<T>::value) t = T(0.5) / zeta;
-        else t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-        const T cs = T(1) / sqrt(T(1) + t * t), sn = t * cs;
+        // rotation parameters in FP64 whatever T is: unbiased c, s, u keep
+        // the accumulated U unitary over many sweeps
+        const double agd = hypot((double)gr, (double)gi);
+        const double thr = fmax((double)tol_rel * sqrt((double)a * (double)b), (double)floor_abs);
+        if (!(agd > thr) || agd == 0.0) continue;
+        const double zeta = ((double)b - (double)a) / (2.0 * agd);
+        double td;
+        if (fabs(zeta) > 1e16) td = 0.5 / zeta;
+        else td = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double csd = 1.0 / sqrt(1.0 + td * td);
+        const T cs = (T)csd, sn = (T)(td * csd);
         if (sn == T(0)) continue;
-        const T ur = gr / ag, ui = gi / ag;
+        const T ur = (T)((double)gr / agd), ui = (T)((double)gi / agd);
         if (lane == 0) atomicAdd(&ctl->active[sweep], 1);
         for (int j = lane; j < c; j += 32) {
           const cplx<T> x = ldcg(&xp[j]), y = ldcg(&xq[j]);
@@ -568,5 +572,273 @@ __global__ void conj_transpose_kernel(const cplx<T>* __restrict__ in, int r, int
   for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
     const int j = bx + yy, i = by + threadIdx.x;
     if (j < c && i < r) out[(size_t)j * ldo + i] = cconj<T>(tile[threadIdx.x][yy]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Block one-sided Jacobi SVD (row blocks of JB rows; a pair holds 2 JB rows).
+// Same contract as onesided_jacobi_kernel: X (r x c) <- U^H X with rows
+// mutually orthogonal, Ut = U^T, w = squared row norms.
+//
+// Rows are grouped in nb = ceil(r / JB) blocks, paired round-robin (bye for
+// odd nb). For the pair (P, Q) of a round:
+//   G = X_PQ X_PQ^H (2JB x 2JB), diagonalised as G = J diag J^H by an in-CTA
+//   cyclic Jacobi, then X_PQ <- J^H X_PQ and Ut_PQ <- J^T Ut_PQ;
+// this orthogonalises all 2JB rows of the pair at once (block Jacobi; the
+// rotations are applied as small dense products, so each round streams X once
+// instead of once per row pair). A pair is left alone when every cross entry
+// satisfies |G_ij| <= max(tol sqrt(G_ii G_jj), floor * max_k G_kk).
+// One round = three phases of a persistent cooperative launch:
+//   G: Gram partials over column chunks (pair x chunk work items)   barrier
+//   E: per pair, sum partials, skip test, inner Jacobi -> J         barrier
+//   A: per pair x chunk, apply J to X and to Ut                     barrier
+// ---------------------------------------------------------------------------
+constexpr int JB = 16;           // rows per block
+constexpr int JP = 2 * JB;       // rows per pair
+constexpr int JCW = 256;         // columns per Gram / apply work item
+
+
+// In-CTA cyclic Jacobi of the pair's 2JB x 2JB Gram, always in FP64 (the
+// matrix is tiny; FP64 keeps the accumulated rotation J unitary to ~1e-16 so
+// that no rounding drift builds up over the many rounds that reuse U).
+__device__ void bj_inner_eig(double2* Gs /*JP x JP, ld JP+1*/, double2* Vs /*JP x JP, ld JP+1*/, double tol,
+                             int max_sweeps) {
+  constexpr int LD = JP + 1;
+  __shared__ double rc[JP / 2], rs[JP / 2], rur[JP / 2], rui[JP / 2];
+  __shared__ int s_act;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < JP * JP; e += blockDim.x) {
+    const int i = e / JP, j = e % JP;
+    Vs[i * LD + j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  for (int sw = 0; sw < max_sweeps; ++sw) {
+    if (tid == 0) s_act = 0;
+    __syncthreads();
+    for (int rd = 0; rd < JP - 1; ++rd) {
+      if (tid < JP / 2) {
+        int p = rr_player(tid, rd, JP), q = rr_player(JP - 1 - tid, rd, JP);
+        if (p > q) { int t_ = p; p = q; q = t_; }
+        const double a_ = Gs[p * LD + p].x, b_ = Gs[q * LD + q].x;
+        const double2 g = Gs[p * LD + q];
+        const double ag = hypot(g.x, g.y);
+        double c_ = 1.0, s_ = 0.0, ur = 1.0, ui = 0.0;
+        if (ag > tol * sqrt(fabs(a_ * b_)) && ag > 0.0) {
+          const double zeta = (b_ - a_) / (2.0 * ag);
+          double t;
+          if (fabs(zeta) > 1e16) t = 0.5 / zeta;
+          else t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          c_ = 1.0 / sqrt(1.0 + t * t);
+          s_ = t * c_;
+          ur = g.x / ag; ui = g.y / ag;
+          if (s_ != 0.0) atomicAdd(&s_act, 1);
+        }
+        rc[tid] = c_; rs[tid] = s_; rur[tid] = ur; rui[tid] = ui;
+      }
+      __syncthreads();
+      for (int e = tid; e < 2 * JP * (JP / 2); e += blockDim.x) {
+        const int pi = e % (JP / 2), row = e / (JP / 2);
+        const double s_ = rs[pi];
+        if (s_ == 0.0) continue;
+        int p = rr_player(pi, rd, JP), q = rr_player(JP - 1 - pi, rd, JP);
+        if (p > q) { int t_ = p; p = q; q = t_; }
+        double2* R = row < JP ? Gs + row * LD : Vs + (row - JP) * LD;
+        const double c_ = rc[pi];
+        const double2 x = R[p], y = R[q];
+        const double2 uy = cmul<double>(make_double2(rur[pi], -rui[pi]), y);
+        R[p] = make_double2(c_ * x.x - s_ * uy.x, c_ * x.y - s_ * uy.y);
+        R[q] = make_double2(s_ * x.x + c_ * uy.x, s_ * x.y + c_ * uy.y);
+      }
+      __syncthreads();
+      for (int e = tid; e < JP * (JP / 2); e += blockDim.x) {
+        const int pi = e % (JP / 2), j = e / (JP / 2);
+        const double s_ = rs[pi];
+        if (s_ == 0.0) continue;
+        int p = rr_player(pi, rd, JP), q = rr_player(JP - 1 - pi, rd, JP);
+        if (p > q) { int t_ = p; p = q; q = t_; }
+        const double c_ = rc[pi];
+        const double2 x = Gs[p * LD + j], y = Gs[q * LD + j];
+        const double2 uy = cmul<double>(make_double2(rur[pi], rui[pi]), y);
+        double2 np_ = make_double2(c_ * x.x - s_ * uy.x, c_ * x.y - s_ * uy.y);
+        double2 nq_ = make_double2(s_ * x.x + c_ * uy.x, s_ * x.y + c_ * uy.y);
+        if (j == q) np_ = make_double2(0.0, 0.0);
+        if (j == p) { nq_ = make_double2(0.0, 0.0); np_.y = 0.0; }
+        if (j == q) nq_.y = 0.0;
+        Gs[p * LD + j] = np_;
+        Gs[q * LD + j] = nq_;
+      }
+      __syncthreads();
+    }
+    const int act = s_act;
+    __syncthreads();
+    if (act == 0) break;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, int c, int ldx, cplx<T>* Ut, T* w,
+                                                            cplx<T>* Gpart, cplx<T>* Jbuf, int* act_flag, OSCtl* ctl,
+                                                            int max_sweeps, T tol_rel, T floor_rel, long long timeout_ns) {
+  constexpr int LD = JP + 1;
+  __shared__ double2 Gs[JP * LD];     // phase E: the pair Gram in FP64; phase A: J in T
+  __shared__ double2 Vs[JP * LD];
+  __shared__ cplx<T> tileX[JP][17];
+  cplx<T>* Js = reinterpret_cast<cplx<T>*>(Gs);
+  __shared__ T s_floor;
+  const int nb = (r + JB - 1) / JB, N = nb + (nb & 1), npairs = N / 2;
+  const int nch = (c + JCW - 1) / JCW, nchu = (r + JCW - 1) / JCW;
+  const unsigned nblk = gridDim.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwb = blockDim.x >> 5;
+  const long gwarp = (long)blockIdx.x * nwb + warp, nwarps = (long)nblk * nwb;
+  const size_t gtid = (size_t)blockIdx.x * blockDim.x + tid, gthreads = (size_t)nblk * blockDim.x;
+  if (max_sweeps > 64) max_sweeps = 64;
+
+  for (size_t e = gtid; e < (size_t)r * r; e += gthreads) {
+    const size_t i = e / r, j = e % r;
+    stcg(&Ut[e], mk<T>(i == j ? T(1) : T(0), T(0)));
+  }
+  for (long i = gwarp; i < r; i += nwarps) {
+    T s = T(0);
+    for (int j = lane; j < c; j += 32) { const cplx<T> x = ldcg(&X[(size_t)i * ldx + j]); s += x.x * x.x + x.y * x.y; }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) w[i] = s;
+  }
+  if (!grid_barrier(&ctl->g, nblk, timeout_ns)) return;
+  if (tid == 0) {
+    T mx = T(0);
+    for (int i = 0; i < r; ++i) mx = fmax(mx, __ldcg(&w[i]));
+    s_floor = floor_rel * mx;
+  }
+  __syncthreads();
+  const T floor_abs = s_floor;
+
+  int sweep = 0;
+  bool converged = (r <= 1);
+  for (; sweep < max_sweeps && !converged; ++sweep) {
+    for (int rd = 0; rd < N - 1; ++rd) {
+      unsigned long long tph = (blockIdx.x == 0 && tid == 0) ? global_timer_ns() : 0ull;
+      // ---- phase G: partial Grams of each pair over column chunks ---------
+      for (long item = blockIdx.x; item < (long)npairs * nch; item += nblk) {
+        const int pi = (int)(item / nch), ch = (int)(item % nch);
+        int P = rr_player(pi, rd, N), Q = rr_player(N - 1 - pi, rd, N);
+        if (P > Q) { int t_ = P; P = Q; Q = t_; }
+        if (Q >= nb) continue;
+        // thread (ti, tj) owns G[2ti..2ti+1][2tj..2tj+1]; 16 x 16 threads
+        const int ti = tid >> 4, tj = tid & 15;
+        cplx<T> acc[2][2] = {{czero<T>(), czero<T>()}, {czero<T>(), czero<T>()}};
+        const int c0 = ch * JCW, c1 = min(c, c0 + JCW);
+        for (int k0 = c0; k0 < c1; k0 += 16) {
+          for (int e = tid; e < JP * 16; e += blockDim.x) {
+            const int i = e >> 4, k = e & 15;
+            const int row = (i < JB ? P * JB + i : Q * JB + (i - JB));
+            cplx<T> v = czero<T>();
+            if (row < r && k0 + k < c1) v = ldcg(&X[(size_t)row * ldx + k0 + k]);
+            tileX[i][k] = v;
+          }
+          __syncthreads();
+#pragma unroll 4
+          for (int k = 0; k < 16; ++k) {
+            const cplx<T> a0 = tileX[2 * ti][k], a1 = tileX[2 * ti + 1][k];
+            const cplx<T> b0 = cconj<T>(tileX[2 * tj][k]), b1 = cconj<T>(tileX[2 * tj + 1][k]);
+            cfma<T>(acc[0][0], a0, b0); cfma<T>(acc[0][1], a0, b1);
+            cfma<T>(acc[1][0], a1, b0); cfma<T>(acc[1][1], a1, b1);
+          }
+          __syncthreads();
+        }
+        cplx<T>* Gp = Gpart + ((size_t)pi * nch + ch) * JP * JP;
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+          for (int b = 0; b < 2; ++b) stcg(&Gp[(2 * ti + a) * JP + 2 * tj + b], acc[a][b]);
+      }
+      if (!grid_barrier(&ctl->g, nblk, timeout_ns)) return;
+      if (blockIdx.x == 0 && tid == 0) { unsigned long long t2 = global_timer_ns(); ctl->phase_ns[0] += t2 - tph; tph = t2; }
+      // ---- phase E: per pair, reduce, test, inner eigen-solve ---------------
+      for (long pi = blockIdx.x; pi < npairs; pi += nblk) {
+        int P = rr_player((int)pi, rd, N), Q = rr_player(N - 1 - (int)pi, rd, N);
+        if (P > Q) { int t_ = P; P = Q; Q = t_; }
+        if (Q >= nb) { if (tid == 0) act_flag[pi] = 0; continue; }
+        for (int e = tid; e < JP * JP; e += blockDim.x) {
+          double sr = 0.0, si = 0.0;
+          for (int ch = 0; ch < nch; ++ch) {
+            const cplx<T> v = ldcg(&Gpart[((size_t)pi * nch + ch) * JP * JP + e]);
+            sr += (double)v.x; si += (double)v.y;
+          }
+          Gs[(e / JP) * LD + (e % JP)] = make_double2(sr, si);
+        }
+        __shared__ int s_need;
+        if (tid == 0) s_need = 0;
+        __syncthreads();
+        for (int e = tid; e < JB * JB; e += blockDim.x) {
+          const int i = e / JB, j = JB + e % JB;
+          const double aij = hypot(Gs[i * LD + j].x, Gs[i * LD + j].y);
+          const double thr = fmax((double)tol_rel * sqrt(fabs(Gs[i * LD + i].x * Gs[j * LD + j].x)), (double)floor_abs);
+          if (aij > thr) s_need = 1;
+        }
+        __syncthreads();
+        const int need = s_need;
+        if (need) {
+          bj_inner_eig(Gs, Vs, 1e-14, 15);
+          for (int e = tid; e < JP * JP; e += blockDim.x) {
+            const double2 v = Vs[(e / JP) * LD + (e % JP)];
+            stcg(&Jbuf[(size_t)pi * JP * JP + e], mk<T>((T)v.x, (T)v.y));
+          }
+          if (tid == 0) { act_flag[pi] = 1; atomicAdd(&ctl->active[sweep], 1); }
+        } else if (tid == 0) {
+          act_flag[pi] = 0;
+        }
+        __syncthreads();
+      }
+      if (!grid_barrier(&ctl->g, nblk, timeout_ns)) return;
+      if (blockIdx.x == 0 && tid == 0) { unsigned long long t2 = global_timer_ns(); ctl->phase_ns[1] += t2 - tph; tph = t2; }
+      // ---- phase A: X_PQ <- J^H X_PQ, Ut_PQ <- J^T Ut_PQ -----------------
+      for (long item = blockIdx.x; item < (long)npairs * (nch + nchu); item += nblk) {
+        const int pi = (int)(item / (nch + nchu)), ch = (int)(item % (nch + nchu));
+        if (!__ldcg(&act_flag[pi])) continue;
+        int P = rr_player(pi, rd, N), Q = rr_player(N - 1 - pi, rd, N);
+        if (P > Q) { int t_ = P; P = Q; Q = t_; }
+        const bool onU = ch >= nch;
+        cplx<T>* M = onU ? Ut : X;
+        const int ld = onU ? r : ldx, ncol = onU ? r : c;
+        const int c0 = (onU ? ch - nch : ch) * JCW, c1 = min(ncol, c0 + JCW);
+        for (int e = tid; e < JP * JP; e += blockDim.x) {
+          // Gs[i][k] = (J^H)[i][k] = conj(J[k][i])  or  (J^T)[i][k] = J[k][i]
+          const int i = e / JP, k = e % JP;
+          const cplx<T> v = ldcg(&Jbuf[(size_t)pi * JP * JP + k * JP + i]);
+          Js[i * LD + k] = onU ? v : cconj<T>(v);
+        }
+        __syncthreads();
+        for (int col = c0 + tid; col < c1; col += blockDim.x) {
+          cplx<T> xin[JP];
+#pragma unroll
+          for (int k = 0; k < JP; ++k) {
+            const int row = (k < JB ? P * JB + k : Q * JB + (k - JB));
+            xin[k] = row < r ? ldcg(&M[(size_t)row * ld + col]) : czero<T>();
+          }
+#pragma unroll 2
+          for (int i = 0; i < JP; ++i) {
+            const int row = (i < JB ? P * JB + i : Q * JB + (i - JB));
+            cplx<T> acc = czero<T>();
+#pragma unroll
+            for (int k = 0; k < JP; ++k) cfma<T>(acc, Js[i * LD + k], xin[k]);
+            if (row < r) stcg(&M[(size_t)row * ld + col], acc);
+          }
+        }
+        __syncthreads();
+      }
+      if (!grid_barrier(&ctl->g, nblk, timeout_ns)) return;
+      if (blockIdx.x == 0 && tid == 0) ctl->phase_ns[2] += global_timer_ns() - tph;
+    }
+    if (atomicAdd(&ctl->active[sweep], 0) == 0) converged = true;
+  }
+  for (long i = gwarp; i < r; i += nwarps) {
+    T s = T(0);
+    for (int j = lane; j < c; j += 32) { const cplx<T> x = ldcg(&X[(size_t)i * ldx + j]); s += x.x * x.x + x.y * x.y; }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) w[i] = s;
+  }
+  if (gtid == 0) {
+    ctl->g.sweeps = sweep;
+    ctl->g.status = converged ? 0 : 1;
   }
 }

@@ -46,6 +46,7 @@ thread_local std::string g_last_init_error;
 struct HostSync {   // pinned read-back of the last select + eigen-solve
   SelectInfo info;
   GridCtl ctl;
+  unsigned long long phase_ns[4];
 };
 
 }  // namespace
@@ -73,6 +74,9 @@ struct mpo_ctx {
   SelectInfo* info = nullptr;
   GridCtl* ctl = nullptr;
   OSCtl* osctl = nullptr;
+  void *bj_gpart = nullptr, *bj_j = nullptr;   // block Jacobi workspaces
+  int* bj_act = nullptr;
+  int block_min_rows = 0;
   double* scal = nullptr;          // [0] lognorm, [1] discarded accumulator
   double* dS = nullptr;            // [n-1]
   double* dschmidt = nullptr;      // [(n-1) * chi_max]
@@ -86,6 +90,62 @@ struct mpo_ctx {
   int centre = 0;
   size_t bytes = 0;
   int last_sweeps = 0;
+  // kernel-class timing (mpo_profile): CUDA events recorded on h->st around
+  // each launch, resolved lazily
+  bool prof = false;
+  struct Pending { int cls; cudaEvent_t a, b; double flops, bytes; };
+  std::vector<Pending> pend;
+  std::vector<cudaEvent_t> evpool;
+  double prof_ms[8] = {0}, prof_flops[8] = {0}, prof_bytes[8] = {0};
+  long long prof_n[8] = {0};
+  long long prof_sweeps = 0;
+  double prof_phase_ns[3] = {0, 0, 0};
+};
+
+enum { PK_SVD = 0, PK_GEMM, PK_SUPEROP, PK_SELECT, PK_GATHER, PK_TRANSPOSE, PK_TRACE, PK_NCLASS };
+static const char* kProfNames[PK_NCLASS] = {"svd_jacobi", "cgemm", "superop", "select", "gather", "transpose", "trace"};
+
+static cudaEvent_t prof_event(mpo_ctx* h) {
+  if (!h->evpool.empty()) { cudaEvent_t e = h->evpool.back(); h->evpool.pop_back(); return e; }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+static void prof_resolve(mpo_ctx* h) {
+  if (h->pend.empty()) return;
+  cudaStreamSynchronize(h->st);
+  for (auto& q : h->pend) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) {
+      h->prof_ms[q.cls] += ms;
+      h->prof_n[q.cls] += 1;
+      h->prof_flops[q.cls] += q.flops;
+      h->prof_bytes[q.cls] += q.bytes;
+    }
+    h->evpool.push_back(q.a);
+    h->evpool.push_back(q.b);
+  }
+  h->pend.clear();
+}
+
+// Bracket one launch with events when profiling is on.
+struct ProfScope {
+  mpo_ctx* h;
+  int cls;
+  double flops, bytes;
+  cudaEvent_t a = nullptr;
+  ProfScope(mpo_ctx* h_, int c, double f, double b) : h(h_), cls(c), flops(f), bytes(b) {
+    if (h->prof) { a = prof_event(h); cudaEventRecord(a, h->st); }
+  }
+  void set(double f, double b) { flops = f; bytes = b; }
+  ~ProfScope() {
+    if (!h->prof || !a) return;
+    cudaEvent_t b = prof_event(h);
+    cudaEventRecord(b, h->st);
+    h->pend.push_back({cls, a, b, flops, bytes});
+    if (h->pend.size() > 2048) prof_resolve(h);
+  }
 };
 
 // ------------------------------------------------------------------ errors --
@@ -160,7 +220,9 @@ static cudaError_t launch_onesided(cudaStream_t st, cplx<T>* X, int r, int c, in
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int N = r + (r & 1);
-  const int want = std::max(1, (N / 2 + 7) / 8);   // one warp per pair
+  // one warp per pair; at least one CTA per SM so that the FP64 units of every
+  // SM take part even when the pairs are few
+  const int want = std::max(num_sms, (N / 2 + 7) / 8);
   const int blocks = std::max(1, std::min(per_sm * num_sms, want));
   e = cudaMemsetAsync(ctl, 0, sizeof(OSCtl), st);
   if (e != cudaSuccess) return e;
@@ -173,21 +235,61 @@ static cudaError_t launch_onesided(cudaStream_t st, cplx<T>* X, int r, int c, in
   return cudaLaunchCooperativeKernel((const void*)onesided_jacobi_kernel<T>, dim3(blocks), dim3(256), args, 0, st);
 }
 
+template <typename T>
+static cudaError_t launch_block_jacobi(cudaStream_t st, cplx<T>* X, int r, int c, int ldx, cplx<T>* Ut, T* w,
+                                      cplx<T>* Gpart, cplx<T>* Jbuf, int* act, OSCtl* ctl, int max_sweeps,
+                                      double timeout_s, int num_sms) {
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, block_jacobi_kernel<T>, 256, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int nb = (r + JB - 1) / JB, npairs = (nb + (nb & 1)) / 2;
+  const int items = npairs * ((c + JCW - 1) / JCW + (r + JCW - 1) / JCW);
+  const int blocks = std::max(1, std::min(per_sm * num_sms, items));
+  e = cudaMemsetAsync(ctl, 0, sizeof(OSCtl), st);
+  if (e != cudaSuccess) return e;
+  const T tol_rel = (T)(2.0 * eps_of<T>::value * std::sqrt((double)std::max(c, 1)));
+  const T floor_rel = (T)(2.0 * eps_of<T>::value * std::sqrt((double)std::max(c, 1)));
+  long long timeout_ns = (long long)(timeout_s * 1e9);
+  void* args[] = {&X, &r, &c, &ldx, &Ut, &w, &Gpart, &Jbuf, &act, &ctl, &max_sweeps, (void*)&tol_rel,
+                  (void*)&floor_rel, &timeout_ns};
+  return cudaLaunchCooperativeKernel((const void*)block_jacobi_kernel<T>, dim3(blocks), dim3(256), args, 0, st);
+}
+
 // One-sided Jacobi SVD of X (r x c, rows orthogonalised in place; left factor
 // transposed in h->vecs), then select the kept squared singular values; waits
 // for the stream and returns the kept count in *k (or an error code).
 template <typename T>
 static int svd_select(mpo_ctx* h, cplx<T>* X, int r, int c, int ldx, int cap, bool disc, double* S, double* sch, int* k) {
   T* w = (T*)h->wv;
-  CK(h, launch_onesided<T>(h->st, X, r, c, ldx, (cplx<T>*)h->vecs, w, h->osctl, h->opts.eig_max_sweeps,
-                           h->opts.barrier_timeout_s, h->num_sms));
-  CK(h, launch_select<T>(h->st, w, r, cap, h->cutoff * h->cutoff, h->perm, h->lam2, h->info,
-                         disc ? h->scal + 1 : nullptr, h->scal, S, sch));
+  {
+    // algorithmic work of the factorisation: Hermitian Gram of the short side
+    // (4 mn^2 mx real flops) plus its dense eigen-decomposition (13.3 mn^3);
+    // bytes: read and write X, write U
+    const double mn = std::min(r, c), mx = std::max(r, c);
+    ProfScope ps(h, PK_SVD, 4.0 * mn * mn * mx + 13.3 * mn * mn * mn,
+                 (2.0 * r * c + (double)r * r) * sizeof(cplx<T>));
+    if (h->block_min_rows > 0 && r >= h->block_min_rows)
+      CK(h, launch_block_jacobi<T>(h->st, X, r, c, ldx, (cplx<T>*)h->vecs, w, (cplx<T>*)h->bj_gpart,
+                                   (cplx<T>*)h->bj_j, h->bj_act, h->osctl, h->opts.eig_max_sweeps,
+                                   h->opts.barrier_timeout_s, h->num_sms));
+    else
+      CK(h, launch_onesided<T>(h->st, X, r, c, ldx, (cplx<T>*)h->vecs, w, h->osctl, h->opts.eig_max_sweeps,
+                               h->opts.barrier_timeout_s, h->num_sms));
+  }
+  {
+    ProfScope ps(h, PK_SELECT, 0.0, (double)r * (sizeof(T) + sizeof(int) + sizeof(double)));
+    CK(h, launch_select<T>(h->st, w, r, cap, h->cutoff * h->cutoff, h->perm, h->lam2, h->info,
+                           disc ? h->scal + 1 : nullptr, h->scal, S, sch));
+  }
   CK(h, cudaMemcpyAsync(&h->hs->info, h->info, sizeof(SelectInfo), cudaMemcpyDeviceToHost, h->st));
   CK(h, cudaMemcpyAsync(&h->hs->ctl, &h->osctl->g, sizeof(GridCtl), cudaMemcpyDeviceToHost, h->st));
+  if (h->prof) CK(h, cudaMemcpyAsync(h->hs->phase_ns, h->osctl->phase_ns, sizeof(h->hs->phase_ns), cudaMemcpyDeviceToHost, h->st));
   CK(h, cudaStreamSynchronize(h->st));
+  if (h->prof) for (int i = 0; i < 3; ++i) h->prof_phase_ns[i] += h->hs->phase_ns[i];
   if (h->hs->ctl.err) return fail(h, MPO_ERR_TIMEOUT, "grid barrier wait timed out in the SVD");
   h->last_sweeps = h->hs->ctl.sweeps;
+  h->prof_sweeps += h->prof ? h->hs->ctl.sweeps : 0;
   if (h->hs->ctl.status)
     return fail(h, MPO_ERR_NOCONV, "Jacobi SVD reached eig_max_sweeps (" + std::to_string(r) + " x " + std::to_string(c) + ")");
   *k = h->hs->info.k;
@@ -196,11 +298,19 @@ static int svd_select(mpo_ctx* h, cplx<T>* X, int r, int c, int ldx, int cap, bo
 
 template <typename T> static cplx<T>* S_(mpo_ctx* h, int k) { return (cplx<T>*)h->site[k]; }
 
+template <typename T>
+static cudaError_t gemm_p(mpo_ctx* h, int M, int N, int K, const cplx<T>* A, int lda, int opA, const cplx<T>* B,
+                          int ldb, int opB, cplx<T>* C, int ldc, const double* alpha_dev = nullptr) {
+  ProfScope ps(h, PK_GEMM, 8.0 * M * N * K, (double)((size_t)M * K + (size_t)K * N + (size_t)M * N) * sizeof(cplx<T>));
+  return cgemm<T>(h->st, M, N, K, A, lda, opA, B, ldb, opB, C, ldc, alpha_dev, 1.0);
+}
+
 static void swap_spare(mpo_ctx* h, int k) { std::swap(h->site[k], h->spare); }
 
 template <typename T>
 static cudaError_t gather_rows(mpo_ctx* h, const cplx<T>* src, int lds, int len, int k, int transpose, int conj_,
                                int mode, cplx<T>* out, int ldo) {
+  ProfScope ps(h, PK_GATHER, 0.0, 2.0 * len * k * sizeof(cplx<T>));
   gather_rows_kernel<T><<<grid_for((size_t)len * k, h->num_sms), 256, 0, h->st>>>(
       src, lds, len, h->perm, h->lam2, h->info, k, transpose, conj_, mode, out, ldo);
   return cudaGetLastError();
@@ -208,6 +318,7 @@ static cudaError_t gather_rows(mpo_ctx* h, const cplx<T>* src, int lds, int len,
 
 template <typename T>
 static cudaError_t conj_transpose(mpo_ctx* h, const cplx<T>* in, int r, int c, int ldi, cplx<T>* out, int ldo) {
+  ProfScope ps(h, PK_TRANSPOSE, 0.0, 2.0 * r * c * sizeof(cplx<T>));
   dim3 grid((c + 31) / 32, (r + 31) / 32);
   conj_transpose_kernel<T><<<grid, dim3(32, 8), 0, h->st>>>(in, r, c, ldi, out, ldo);
   return cudaGetLastError();
@@ -228,7 +339,7 @@ static int move_right(mpo_ctx* h, int k) {
   CK(h, gather_rows<T>(h, Y, mX, mX, rk, 1, 1, 1, (cplx<T>*)h->spare, rk));     // Q (mX x rk)
   swap_spare(h, k);
   CK(h, gather_rows<T>(h, (cplx<T>*)h->vecs, r, r, rk, 0, 1, 2, tmp, r));         // R (rk x r)
-  CK(h, cgemm<T>(h->st, rk, mR, r, tmp, r, 0, S_<T>(h, k + 1), mR, 0, (cplx<T>*)h->spare, mR));
+  CK(h, gemm_p<T>(h, rk, mR, r, tmp, r, 0, S_<T>(h, k + 1), mR, 0, (cplx<T>*)h->spare, mR));
   swap_spare(h, k + 1);
   h->chi[k + 1] = rk;
   h->centre = k + 1;
@@ -252,7 +363,7 @@ static int move_left(mpo_ctx* h, int k, bool record) {
   CK(h, gather_rows<T>(h, Y, mR, mR, rk, 0, 0, 1, (cplx<T>*)h->spare, mR));        // Lambda^-1 X'
   swap_spare(h, k);
   CK(h, gather_rows<T>(h, (cplx<T>*)h->vecs, r, r, rk, 1, 0, 2, tmp, rk));          // U Lambda / ||kept||
-  CK(h, cgemm<T>(h->st, mL, rk, r, S_<T>(h, k - 1), r, 0, tmp, rk, 0, (cplx<T>*)h->spare, rk));
+  CK(h, gemm_p<T>(h, mL, rk, r, S_<T>(h, k - 1), r, 0, tmp, rk, 0, (cplx<T>*)h->spare, rk));
   swap_spare(h, k - 1);
   h->chi[k] = rk;
   h->centre = k - 1;
@@ -280,9 +391,12 @@ static int gate_update(mpo_ctx* h, int i, const cplx<T>* M) {
   cplx<T>* A0 = S_<T>(h, i);
   cplx<T>* A1 = S_<T>(h, i + 1);
   cplx<T>* th = (cplx<T>*)h->theta;
-  CK(h, cgemm<T>(h->st, mL, mR, chiM, A0, chiM, 0, A1, mR, 0, th, mR));        // theta
-  apply_superop_kernel<T><<<grid_for((size_t)chiL * chiR, h->num_sms), 256, 0, h->st>>>(th, chiL, chiR, M);
-  CK(h, cudaGetLastError());
+  CK(h, gemm_p<T>(h, mL, mR, chiM, A0, chiM, 0, A1, mR, 0, th, mR));        // theta
+  {
+    ProfScope ps(h, PK_SUPEROP, 2048.0 * chiL * chiR, 32.0 * chiL * chiR * sizeof(cplx<T>));
+    apply_superop_kernel<T><<<grid_for((size_t)chiL * chiR, h->num_sms), 256, 0, h->st>>>(th, chiL, chiR, M);
+    CK(h, cudaGetLastError());
+  }
   int k = 0;
   if (mL <= mR) {
     // theta' = U X', rows of X' = Lambda W^H
@@ -377,8 +491,11 @@ static int trace_t(mpo_ctx* h, double* tr) {
   double2 *a = h->tv0, *b = h->tv1;
   for (int k = 0; k < h->n; ++k) {
     const int cl = h->chi[k], cr = h->chi[k + 1];
-    trace_step_kernel<T><<<(cr + 127) / 128, 128, 0, h->st>>>(S_<T>(h, k), cl, cr, a, b);
-    CK(h, cudaGetLastError());
+    {
+      ProfScope ps(h, PK_TRACE, 8.0 * cl * cr, (2.0 * cl * cr) * sizeof(cplx<T>));
+      trace_step_kernel<T><<<(cr + 127) / 128, 128, 0, h->st>>>(S_<T>(h, k), cl, cr, a, b);
+      CK(h, cudaGetLastError());
+    }
     std::swap(a, b);
   }
   double2 v;
@@ -400,6 +517,7 @@ void mpo_default_opts(mpo_opts* o) {
   o->arena_cap_bytes = 0;
   o->smode = MPO_S_ALL_BONDS;
   o->barrier_timeout_s = 5.0;
+  o->block_jacobi_min_rows = 0;
 }
 
 const char* mpo_version(void) { return "gb300-mpo 0.1 (sm_103a)"; }
@@ -457,6 +575,10 @@ int mpo_init(mpo_handle* out, int n, int chi_max, mpo_precision prec, void* stre
   const int jac_limit = prec == MPO_FP64 ? 8192 : 16384;   // rotation table must fit shared memory
   if (m > jac_limit) return init_fail(h, MPO_ERR_ARG, "bond dimension too large for the eigen-solver's shared-memory table");
   h->tmp_cap = (size_t)m * chi_max;
+  h->block_min_rows = h->opts.block_jacobi_min_rows < 0 ? 0
+                      : (h->opts.block_jacobi_min_rows > 0 ? h->opts.block_jacobi_min_rows : (prec == MPO_FP32 ? 64 : 0));
+  const size_t bj_pairs = (size_t)((m + JB - 1) / JB + 1) / 2 + 1;
+  const size_t bj_nch = (size_t)(4 * chi_max + JCW - 1) / JCW + 1;
   const int ngmax = n / 2;
   const size_t need = (size_t)(n + 1) * h->site_cap * h->esz + 2 * th * h->esz + (size_t)m * m * h->esz +
                       h->tmp_cap * h->esz + (size_t)m * (rsz + sizeof(int) + sizeof(double)) +
@@ -491,6 +613,11 @@ int mpo_init(mpo_handle* out, int n, int chi_max, mpo_precision prec, void* stre
   ok = ok && alloc((void**)&h->info, sizeof(SelectInfo));
   ok = ok && alloc((void**)&h->ctl, sizeof(GridCtl));
   ok = ok && alloc((void**)&h->osctl, sizeof(OSCtl));
+  if (h->block_min_rows > 0) {
+    ok = ok && alloc(&h->bj_gpart, bj_pairs * bj_nch * JP * JP * h->esz);
+    ok = ok && alloc(&h->bj_j, bj_pairs * JP * JP * h->esz);
+    ok = ok && alloc((void**)&h->bj_act, bj_pairs * sizeof(int));
+  }
   ok = ok && alloc((void**)&h->scal, 4 * sizeof(double));
   ok = ok && alloc((void**)&h->dS, (size_t)(n - 1) * sizeof(double));
   ok = ok && alloc((void**)&h->dschmidt, (size_t)(n - 1) * chi_max * sizeof(double));
@@ -531,10 +658,12 @@ int mpo_init(mpo_handle* out, int n, int chi_max, mpo_precision prec, void* stre
 void mpo_free(mpo_handle h) {
   if (!h) return;
   for (void* p : h->site) if (p) cudaFree(p);
-  void* ps[] = {h->spare, h->theta, h->theta2, h->osctl, h->vecs, h->tmp, h->wv, h->perm, h->lam2, h->Ms, h->dgates,
+  void* ps[] = {h->spare, h->theta, h->theta2, h->osctl, h->bj_gpart, h->bj_j, h->bj_act, h->vecs, h->tmp, h->wv, h->perm, h->lam2, h->Ms, h->dgates,
                 h->dsup, h->dp, h->info, h->ctl, h->scal, h->dS, h->dschmidt, h->tv0, h->tv1};
   for (void* p : ps) if (p) cudaFree(p);
   if (h->hs) cudaFreeHost(h->hs);
+  for (auto& q : h->pend) { cudaEventDestroy(q.a); cudaEventDestroy(q.b); }
+  for (auto e : h->evpool) cudaEventDestroy(e);
   delete h;
 }
 
@@ -637,6 +766,40 @@ int mpo_centre(mpo_handle h, int* c) {
 
 size_t mpo_device_bytes(mpo_handle h) { return h ? h->bytes : 0; }
 
+int mpo_profile(mpo_handle h, int enable) {
+  GUARD(h);
+  prof_resolve(h);
+  if (enable) {
+    for (int i = 0; i < PK_NCLASS; ++i) { h->prof_ms[i] = 0; h->prof_n[i] = 0; h->prof_flops[i] = 0; h->prof_bytes[i] = 0; }
+    h->prof_sweeps = 0;
+    for (int i = 0; i < 3; ++i) h->prof_phase_ns[i] = 0;
+  }
+  h->prof = enable != 0;
+  return MPO_OK;
+}
+
+int mpo_profile_read(mpo_handle h, int cls, const char** name, double* ms, long long* launches, double* flops,
+                     double* bytes) {
+  GUARD(h);
+  if (cls < 0 || cls >= PK_NCLASS) return MPO_ERR_ARG;
+  prof_resolve(h);
+  if (name) *name = kProfNames[cls];
+  if (ms) *ms = h->prof_ms[cls];
+  if (launches) *launches = h->prof_n[cls];
+  if (flops) *flops = h->prof_flops[cls];
+  if (bytes) *bytes = h->prof_bytes[cls];
+  return MPO_OK;
+}
+
+long long mpo_profile_sweeps(mpo_handle h) { return h ? h->prof_sweeps : 0; }
+
+int mpo_profile_phases(mpo_handle h, double* ms3) {
+  GUARD(h);
+  if (!ms3) return MPO_ERR_ARG;
+  for (int i = 0; i < 3; ++i) ms3[i] = h->prof_phase_ns[i] * 1e-6;
+  return MPO_OK;
+}
+
 int mpo_get_site(mpo_handle h, int k, double* buf, int* chiL, int* chiR) {
   GUARD(h);
   if (k < 0 || k >= h->n || !chiL || !chiR) return fail(h, MPO_ERR_ARG, "bad site index");
@@ -698,22 +861,38 @@ int mpo_to_dense(mpo_handle h, double* rho_vec) {
   return MPO_OK;
 }
 
-int mpo_svd(int r, int c, void* X, void* w, void* Ut, mpo_precision prec, int max_sweeps, void* stream) {
+int mpo_svd(int r, int c, void* X, void* w, void* Ut, mpo_precision prec, int max_sweeps, int block, void* stream) {
   if (r < 1 || c < 1 || !X || !w || !Ut) return MPO_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return MPO_ERR_CUDA;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   OSCtl* ctl = nullptr;
-  if (cudaMalloc(&ctl, sizeof(OSCtl)) != cudaSuccess) return MPO_ERR_OOM;
+  void *gp = nullptr, *jb = nullptr;
+  int* act = nullptr;
+  const size_t esz = prec == MPO_FP64 ? sizeof(double2) : sizeof(float2);
+  const size_t pairs = (size_t)((r + JB - 1) / JB + 1) / 2 + 1, nch = (size_t)(c + JCW - 1) / JCW + 1;
+  bool ok = cudaMalloc(&ctl, sizeof(OSCtl)) == cudaSuccess;
+  if (block) {
+    ok = ok && cudaMalloc(&gp, pairs * nch * JP * JP * esz) == cudaSuccess;
+    ok = ok && cudaMalloc(&jb, pairs * JP * JP * esz) == cudaSuccess;
+    ok = ok && cudaMalloc((void**)&act, pairs * sizeof(int)) == cudaSuccess;
+  }
+  if (!ok) { cudaGetLastError(); cudaFree(ctl); cudaFree(gp); cudaFree(jb); cudaFree(act); return MPO_ERR_OOM; }
   const int ms = max_sweeps > 0 ? max_sweeps : 40;
-  cudaError_t e = prec == MPO_FP64
-      ? launch_onesided<double>(st, (double2*)X, r, c, c, (double2*)Ut, (double*)w, ctl, ms, 5.0, sms)
-      : launch_onesided<float>(st, (float2*)X, r, c, c, (float2*)Ut, (float*)w, ctl, ms, 5.0, sms);
+  cudaError_t e;
+  if (block)
+    e = prec == MPO_FP64
+        ? launch_block_jacobi<double>(st, (double2*)X, r, c, c, (double2*)Ut, (double*)w, (double2*)gp, (double2*)jb, act, ctl, ms, 5.0, sms)
+        : launch_block_jacobi<float>(st, (float2*)X, r, c, c, (float2*)Ut, (float*)w, (float2*)gp, (float2*)jb, act, ctl, ms, 5.0, sms);
+  else
+    e = prec == MPO_FP64
+        ? launch_onesided<double>(st, (double2*)X, r, c, c, (double2*)Ut, (double*)w, ctl, ms, 5.0, sms)
+        : launch_onesided<float>(st, (float2*)X, r, c, c, (float2*)Ut, (float*)w, ctl, ms, 5.0, sms);
   GridCtl hc{};
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, &ctl->g, sizeof(GridCtl), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  cudaFree(ctl);
+  cudaFree(ctl); cudaFree(gp); cudaFree(jb); cudaFree(act);
   if (e != cudaSuccess) { g_last_init_error = cudaGetErrorString(e); return MPO_ERR_CUDA; }
   if (hc.err) return MPO_ERR_TIMEOUT;
   if (hc.status) return MPO_ERR_NOCONV;

@@ -19,7 +19,8 @@ ERRORS = {0: "MPO_OK", -1: "MPO_ERR_ARG", -2: "MPO_ERR_CUDA", -3: "MPO_ERR_OOM",
           -5: "MPO_ERR_TIMEOUT", -6: "MPO_ERR_STATE"}
 EXPORTS = ["mpo_default_opts", "mpo_init", "mpo_apply_layer", "mpo_apply_gate", "mpo_apply_superop", "mpo_sweep",
            "mpo_entropy", "mpo_schmidt", "mpo_bond_dims", "mpo_get_site", "mpo_to_dense", "mpo_centre",
-           "mpo_device_bytes", "mpo_free", "mpo_last_error", "mpo_eigh", "mpo_svd", "mpo_version"]
+           "mpo_device_bytes", "mpo_free", "mpo_last_error", "mpo_eigh", "mpo_svd", "mpo_version",
+           "mpo_profile", "mpo_profile_read", "mpo_profile_sweeps", "mpo_profile_phases"]
 
 
 class MPOError(RuntimeError):
@@ -31,7 +32,7 @@ class MPOError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("eig_max_sweeps", ctypes.c_int), ("sv_rel_cutoff", ctypes.c_double),
                 ("arena_cap_bytes", ctypes.c_size_t), ("smode", ctypes.c_int),
-                ("barrier_timeout_s", ctypes.c_double)]
+                ("barrier_timeout_s", ctypes.c_double), ("block_jacobi_min_rows", ctypes.c_int)]
 
 
 _lib = None
@@ -65,8 +66,12 @@ def load_library(path: str | None = None):
         "mpo_free": (None, [P]),
         "mpo_last_error": (ctypes.c_char_p, [P]),
         "mpo_eigh": (I, [I, P, P, P, I, I, P]),
-        "mpo_svd": (I, [I, I, P, P, P, I, I, P]),
+        "mpo_svd": (I, [I, I, P, P, P, I, I, I, P]),
         "mpo_version": (ctypes.c_char_p, []),
+        "mpo_profile": (I, [P, I]),
+        "mpo_profile_read": (I, [P, I, ctypes.POINTER(ctypes.c_char_p), DP, ctypes.POINTER(ctypes.c_longlong), DP, DP]),
+        "mpo_profile_sweeps": (ctypes.c_longlong, [P]),
+        "mpo_profile_phases": (I, [P, DP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -104,7 +109,7 @@ class MPO:
 
     def __init__(self, n: int, chi_max: int, precision: str = "fp64", *, cutoff: float = 0.0,
                  eig_max_sweeps: int = 0, arena_cap_bytes: int = 0, centre_only: bool = False,
-                 barrier_timeout_s: float = 0.0, stream=None):
+                 barrier_timeout_s: float = 0.0, block_jacobi_min_rows: int = 0, stream=None):
         lib = load_library()
         self._lib = lib
         self.n, self.chi_max = n, chi_max
@@ -118,6 +123,7 @@ class MPO:
         o.smode = MPO_S_CENTRE if centre_only else MPO_S_ALL_BONDS
         if barrier_timeout_s > 0:
             o.barrier_timeout_s = barrier_timeout_s
+        o.block_jacobi_min_rows = block_jacobi_min_rows
         h = ctypes.c_void_p()
         st = ctypes.c_void_p(stream) if stream is not None else _current_stream()
         rc = lib.mpo_init(ctypes.byref(h), n, chi_max, self.prec, st, ctypes.byref(o))
@@ -189,6 +195,27 @@ class MPO:
         self._check(self._lib.mpo_centre(self.h, ctypes.byref(c)))
         return c.value
 
+    def profile(self, enable: bool = True) -> None:
+        self._check(self._lib.mpo_profile(self.h, int(enable)))
+
+    def profile_read(self) -> dict:
+        """{kernel class: {ms, launches, flops, bytes}} since profile(True)."""
+        out = {}
+        for cls in range(16):
+            nm = ctypes.c_char_p()
+            ms, fl, by = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+            n = ctypes.c_longlong()
+            rc = self._lib.mpo_profile_read(self.h, cls, ctypes.byref(nm), ctypes.byref(ms), ctypes.byref(n),
+                                            ctypes.byref(fl), ctypes.byref(by))
+            if rc != 0:
+                break
+            out[nm.value.decode()] = {"ms": ms.value, "launches": n.value, "flops": fl.value, "bytes": by.value}
+        out["_sweeps"] = int(self._lib.mpo_profile_sweeps(self.h))
+        ph = (ctypes.c_double * 3)()
+        self._check(self._lib.mpo_profile_phases(self.h, ph))
+        out["_block_jacobi_phase_ms"] = {"gram": ph[0], "pair_eig": ph[1], "apply": ph[2]}
+        return out
+
     def device_bytes(self) -> int:
         return int(self._lib.mpo_device_bytes(self.h))
 
@@ -229,7 +256,7 @@ def eigh(A, precision: str = "fp64", max_sweeps: int = 0):
     return w, V
 
 
-def svd_rows(X, precision: str = "fp64", max_sweeps: int = 0):
+def svd_rows(X, precision: str = "fp64", max_sweeps: int = 0, block: bool = False):
     """One-sided Jacobi SVD on the device (test export). X: CUDA tensor (r, c),
     overwritten with U^H X. Returns (w, Ut): squared row norms and U^T."""
     import torch
@@ -239,7 +266,7 @@ def svd_rows(X, precision: str = "fp64", max_sweeps: int = 0):
     rdt = torch.float64 if prec == MPO_FP64 else torch.float32
     w = torch.empty(r, dtype=rdt, device=X.device)
     Ut = torch.empty((r, r), dtype=X.dtype, device=X.device)
-    rc = lib.mpo_svd(r, c, X.data_ptr(), w.data_ptr(), Ut.data_ptr(), prec, max_sweeps,
+    rc = lib.mpo_svd(r, c, X.data_ptr(), w.data_ptr(), Ut.data_ptr(), prec, max_sweeps, int(block),
                      ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     if rc != 0:
         raise MPOError(rc, "mpo_svd failed")
