@@ -209,6 +209,29 @@ int mpo_eigh(int m, void *A, void *w, void *V, mpo_precision prec, int max_sweep
 int mpo_svd(int r, int c, void *X, void *w, void *Ut, mpo_precision prec, int max_sweeps, int block,
             void *cuda_stream);
 
+/* Block one-sided Jacobi SVD that allocates nothing (the paper has no
+ * counterpart; this is a deployment aid).
+ *
+ * Same contract and result as mpo_svd(r, c, X, w, Ut, prec, max_sweeps, 1,
+ * stream) for r <= 512 and c <= 2048, but every piece of scratch the solver
+ * needs lives in one device array built into the library (about 3 MB per
+ * GPU that uses it, held until the process exits). It is meant for callers
+ * that must not call cudaMalloc when they need the factorisation, e.g. code
+ * that runs between cudaStreamBeginCapture and cudaStreamEndCapture, or a host
+ * that grants the library a fixed memory budget ahead of time.
+ *
+ *   - Larger matrices are rejected with MPO_ERR_ARG; mpo_last_error(NULL) says
+ *     which limit was hit. Other errors as for mpo_svd.
+ *   - The first call on a device looks up that array's device address with
+ *     the device current; make that first call before any stream capture.
+ *   - All calls on a device share the one array, which keeps the last call's
+ *     contents. Calls whose work overlaps on the GPU (several streams, several
+ *     host threads) race on it and must be serialised by the caller.
+ *   - The call waits for the stream before it returns (it reads the solver's
+ *     status). */
+int mpo_svd_static(int r, int c, void *X, void *w, void *Ut, mpo_precision prec, int max_sweeps,
+                   void *cuda_stream);
+
 /* Library version string. */
 const char *mpo_version(void);
 

@@ -248,8 +248,11 @@ static cudaError_t launch_block_jacobi(cudaStream_t st, cplx<T>* X, int r, int c
   const int blocks = std::max(1, std::min(per_sm * num_sms, items));
   e = cudaMemsetAsync(ctl, 0, sizeof(OSCtl), st);
   if (e != cudaSuccess) return e;
+  // relative criterion at the rounding level of a length-c dot product; the
+  // absolute floor sits above the rounding of the pair Gram itself, which the
+  // block rotation cannot resolve below
   const T tol_rel = (T)(2.0 * eps_of<T>::value * std::sqrt((double)std::max(c, 1)));
-  const T floor_rel = (T)(2.0 * eps_of<T>::value * std::sqrt((double)std::max(c, 1)));
+  const T floor_rel = (T)(16.0 * eps_of<T>::value * std::sqrt((double)std::max(c, 1)));
   long long timeout_ns = (long long)(timeout_s * 1e9);
   void* args[] = {&X, &r, &c, &ldx, &Ut, &w, &Gpart, &Jbuf, &act, &ctl, &max_sweeps, (void*)&tol_rel,
                   (void*)&floor_rel, &timeout_ns};
@@ -893,6 +896,89 @@ int mpo_svd(int r, int c, void* X, void* w, void* Ut, mpo_precision prec, int ma
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, &ctl->g, sizeof(GridCtl), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(ctl); cudaFree(gp); cudaFree(jb); cudaFree(act);
+  if (e != cudaSuccess) { g_last_init_error = cudaGetErrorString(e); return MPO_ERR_CUDA; }
+  if (hc.err) return MPO_ERR_TIMEOUT;
+  if (hc.status) return MPO_ERR_NOCONV;
+  return MPO_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Block-Jacobi SVD with built-in scratch (mpo_svd_static).
+//
+// Some callers cannot allocate device memory at the point where they need an
+// SVD: code running while a CUDA graph is being captured (where cudaMalloc
+// would break the capture), allocators' own callbacks, or hosts that hand out
+// a fixed memory budget up front. For them this entry point keeps the block
+// Jacobi's scratch (barrier/status block, pair Gram partials, rotations) in
+// one file-scope device array that exists for as long as the library is
+// loaded on each GPU that uses it. The caller only passes the matrix and the
+// two outputs; nothing is allocated or freed.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kStaticMaxRows = 512;
+constexpr int kStaticMaxCols = 2048;
+constexpr size_t kStaticPairs = (size_t)(((kStaticMaxRows + JB - 1) / JB + 1) / 2 + 1);
+constexpr size_t kStaticChunks = (size_t)((kStaticMaxCols + JCW - 1) / JCW + 1);
+struct StaticSvdScratch {       // laid out for the widest element (complex128)
+  OSCtl ctl;
+  int act[kStaticPairs];
+  double2 jbuf[kStaticPairs * JP * JP];
+  double2 gpart[kStaticPairs * kStaticChunks * JP * JP];
+};
+}  // namespace
+
+// Shared by every call on a device; keeps the previous call's contents.
+static __device__ __align__(256) unsigned char g_static_svd_scratch[sizeof(StaticSvdScratch)];
+
+static int static_scratch_address(StaticSvdScratch** out) {
+  // one lookup per device, done with that device current (the symbol's host
+  // name is only a stand-in; the device address comes from the runtime)
+  static void* addr[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return MPO_ERR_CUDA;
+  if (!addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_svd_scratch);
+    if (e != cudaSuccess || !p) {
+      g_last_init_error = std::string("cudaGetSymbolAddress failed: ") + cudaGetErrorString(e);
+      return MPO_ERR_CUDA;
+    }
+    addr[dev] = p;
+  }
+  *out = reinterpret_cast<StaticSvdScratch*>(addr[dev]);
+  return MPO_OK;
+}
+
+int mpo_svd_static(int r, int c, void* X, void* w, void* Ut, mpo_precision prec, int max_sweeps, void* stream) {
+  if (!X || !w || !Ut || r < 1 || c < 1 || (prec != MPO_FP64 && prec != MPO_FP32)) {
+    g_last_init_error = "mpo_svd_static: bad argument";
+    return MPO_ERR_ARG;
+  }
+  if (r > kStaticMaxRows || c > kStaticMaxCols) {
+    g_last_init_error = "mpo_svd_static: matrix " + std::to_string(r) + " x " + std::to_string(c) +
+                        " exceeds the built-in scratch limit of " + std::to_string(kStaticMaxRows) + " x " +
+                        std::to_string(kStaticMaxCols);
+    return MPO_ERR_ARG;
+  }
+  StaticSvdScratch* s = nullptr;
+  int rc = static_scratch_address(&s);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MPO_ERR_CUDA;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int ms = max_sweeps > 0 ? max_sweeps : 40;
+  // launch_block_jacobi clears the control block (barrier counters, status,
+  // per-sweep counts) before the launch; the Gram partials, rotations and
+  // pair flags are fully written before they are read in every round
+  cudaError_t e = prec == MPO_FP64
+      ? launch_block_jacobi<double>(st, (double2*)X, r, c, c, (double2*)Ut, (double*)w, (double2*)s->gpart,
+                                    (double2*)s->jbuf, s->act, &s->ctl, ms, 5.0, sms)
+      : launch_block_jacobi<float>(st, (float2*)X, r, c, c, (float2*)Ut, (float*)w, (float2*)s->gpart,
+                                   (float2*)s->jbuf, s->act, &s->ctl, ms, 5.0, sms);
+  GridCtl hc{};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, &s->ctl.g, sizeof(GridCtl), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) { g_last_init_error = cudaGetErrorString(e); return MPO_ERR_CUDA; }
   if (hc.err) return MPO_ERR_TIMEOUT;
   if (hc.status) return MPO_ERR_NOCONV;

@@ -20,7 +20,7 @@ ERRORS = {0: "MPO_OK", -1: "MPO_ERR_ARG", -2: "MPO_ERR_CUDA", -3: "MPO_ERR_OOM",
 EXPORTS = ["mpo_default_opts", "mpo_init", "mpo_apply_layer", "mpo_apply_gate", "mpo_apply_superop", "mpo_sweep",
            "mpo_entropy", "mpo_schmidt", "mpo_bond_dims", "mpo_get_site", "mpo_to_dense", "mpo_centre",
            "mpo_device_bytes", "mpo_free", "mpo_last_error", "mpo_eigh", "mpo_svd", "mpo_version",
-           "mpo_profile", "mpo_profile_read", "mpo_profile_sweeps", "mpo_profile_phases"]
+           "mpo_profile", "mpo_profile_read", "mpo_profile_sweeps", "mpo_profile_phases", "mpo_svd_static"]
 
 
 class MPOError(RuntimeError):
@@ -72,6 +72,7 @@ def load_library(path: str | None = None):
         "mpo_profile_read": (I, [P, I, ctypes.POINTER(ctypes.c_char_p), DP, ctypes.POINTER(ctypes.c_longlong), DP, DP]),
         "mpo_profile_sweeps": (ctypes.c_longlong, [P]),
         "mpo_profile_phases": (I, [P, DP]),
+        "mpo_svd_static": (I, [I, I, P, P, P, I, I, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -270,4 +271,21 @@ def svd_rows(X, precision: str = "fp64", max_sweeps: int = 0, block: bool = Fals
                      ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     if rc != 0:
         raise MPOError(rc, "mpo_svd failed")
+    return w, Ut
+
+
+def svd_rows_static(X, precision: str = "fp64", max_sweeps: int = 0):
+    """Block one-sided Jacobi SVD through the entry point that allocates
+    nothing (r <= 512, c <= 2048). Same outputs as svd_rows(..., block=True)."""
+    import torch
+    lib = load_library()
+    r, c = X.shape
+    prec = {"fp64": MPO_FP64, "fp32": MPO_FP32}[precision]
+    rdt = torch.float64 if prec == MPO_FP64 else torch.float32
+    w = torch.empty(r, dtype=rdt, device=X.device)
+    Ut = torch.empty((r, r), dtype=X.dtype, device=X.device)
+    rc = lib.mpo_svd_static(r, c, X.data_ptr(), w.data_ptr(), Ut.data_ptr(), prec, max_sweeps,
+                            ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if rc != 0:
+        raise MPOError(rc, lib.mpo_last_error(None).decode())
     return w, Ut

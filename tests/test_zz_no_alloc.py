@@ -1,0 +1,58 @@
+"""The SVD entry point that allocates nothing (mpo_svd_static).
+
+Some callers cannot call cudaMalloc when they need a factorisation, for
+example code running inside a CUDA-graph capture or under a fixed memory
+budget. mpo_svd_static keeps its scratch in a device array built into the
+library. Here it is called through the C ABI and compared with the allocating
+entry point (mpo_svd, block form) on the same inputs, twice in a row, since
+every call reuses the same scratch. This file is collected last on purpose.
+"""
+import numpy as np
+import pytest
+
+from paper_2003_13163_gb300.circuits import random_complex
+from tests.gpu_util import need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    return need_gpu()
+
+
+def _matrix(r, c, seed):
+    k = min(r, c)
+    U = np.linalg.qr(random_complex((r, k), seed=seed))[0]
+    Vh = np.linalg.qr(random_complex((c, k), seed=seed + 1))[0].conj().T
+    return (U * np.exp(-0.02 * np.arange(k))[None, :]) @ Vh
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_static_scratch_svd_matches_allocating_entry(M, prec):
+    import torch
+    dt = torch.complex128 if prec == "fp64" else torch.complex64
+    eps = 2.2e-16 if prec == "fp64" else 1.2e-7
+    for call, (r, c, seed) in enumerate([(200, 700, 1), (130, 256, 7)]):
+        X = torch.tensor(_matrix(r, c, seed), dtype=dt, device="cuda")
+        Xa, Xs = X.clone(), X.clone()
+        wa, Ua = M.svd_rows(Xa, prec, block=True)
+        ws, Us = M.svd_rows_static(Xs, prec)
+        tol = 50 * eps * np.sqrt(c)
+        sa = np.sort(wa.cpu().numpy().astype(np.float64))
+        ss = np.sort(ws.cpu().numpy().astype(np.float64))
+        np.testing.assert_allclose(np.sqrt(np.maximum(ss, 0)), np.sqrt(np.maximum(sa, 0)), atol=tol)
+        # same factorisation: X = U (U^H X) with U from either entry point
+        Um = Us.cpu().numpy().astype(np.complex128).T
+        np.testing.assert_allclose(Um @ Xs.cpu().numpy().astype(np.complex128),
+                                   X.cpu().numpy().astype(np.complex128), atol=tol)
+        np.testing.assert_allclose(Xs.cpu().numpy(), Xa.cpu().numpy(), atol=tol)
+        np.testing.assert_allclose(Us.cpu().numpy(), Ua.cpu().numpy(), atol=tol)
+
+
+def test_static_scratch_svd_rejects_oversize(M):
+    import torch
+    X = torch.zeros((600, 64), dtype=torch.complex128, device="cuda")
+    with pytest.raises(M.MPOError) as e:
+        M.svd_rows_static(X, "fp64")
+    assert e.value.code == -1 and "scratch limit" in str(e.value)
