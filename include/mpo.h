@@ -149,6 +149,24 @@ int mpo_bond_dims(mpo_handle h, int *dims);
  * NULL to query them. */
 int mpo_get_site(mpo_handle h, int k, double *buf, int *chiL, int *chiR);
 
+/* Output probabilities (Sec. 3.4): P(x) = <<X|rho>> with X_k = (d+1) x_k, i.e.
+ * the product over sites of the I = 3 x_k slices, times the tracked scale.
+ *   bits: host [n_strings][n] bytes, each 0 or 1 (x_1 first);
+ *   P   : host [n_strings] out. With truncation P sums to Tr rho <= 1 over all
+ *         x (Sec. 3.4), and single entries can dip slightly below zero.
+ * Synchronises the stream; allocates its scratch per call. */
+int mpo_probability(mpo_handle h, int n_strings, const unsigned char *bits, double *P);
+
+/* Samples from P(x) / Tr rho by sequential conditionals (Sec. 3.4): bit k is 0
+ * when u_k < P(x_1..x_{k-1}, 0) / (P(.., 0) + P(.., 1)), the marginals taken
+ * with the trace vector on the remaining sites; the comparison is made in FP64.
+ *   uniforms: host [n_samples][n] doubles in [0, 1) supplied by the caller
+ *             (the randomness is an input, so runs are reproducible);
+ *   bits    : host [n_samples][n] out;
+ *   P       : nullable host [n_samples] out, P(x) of each drawn string.
+ * Synchronises the stream; allocates its scratch per call. */
+int mpo_sample(mpo_handle h, int n_samples, const double *uniforms, unsigned char *bits, double *P);
+
 /* Contract the MPO into |rho>> (4^n complex128, interleaved, index
  * I_1 I_2 .. I_n with I_1 most significant). n <= 12. Test export. */
 int mpo_to_dense(mpo_handle h, double *rho_vec);

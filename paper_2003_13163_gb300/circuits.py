@@ -106,3 +106,10 @@ def random_complex(shape, seed: int) -> np.ndarray:
     rng = np.random.Generator(np.random.PCG64(seed))
     g = rng.standard_normal((2,) + tuple(shape))
     return (g[0] + 1j * g[1]) / np.sqrt(2.0)
+
+
+def sampling_uniforms(n_samples: int, n: int, seed: int) -> np.ndarray:
+    """Seeded uniforms in [0, 1), shape (n_samples, n): the random input of the
+    sequential-conditional sampler (Sec. 3.4), one per sample and qubit."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.random((n_samples, n))

@@ -477,6 +477,7 @@ __global__ void __launch_bounds__(256) onesided_jacobi_kernel(cplx<T>* X, int r,
         cplx<T>* xp = X + (size_t)p * ldx;
         cplx<T>* xq = X + (size_t)q * ldx;
         T a = T(0), b = T(0), gr = T(0), gi = T(0);
+#pragma unroll 4
         for (int j = lane; j < c; j += 32) {
           const cplx<T> x = ldcg(&xp[j]), y = ldcg(&xq[j]);
           a = fma(x.x, x.x, fma(x.y, x.y, a));
@@ -499,6 +500,7 @@ __global__ void __launch_bounds__(256) onesided_jacobi_kernel(cplx<T>* X, int r,
         if (sn == T(0)) continue;
         const T ur = (T)((double)gr / agd), ui = (T)((double)gi / agd);
         if (lane == 0) atomicAdd(&ctl->active[sweep], 1);
+#pragma unroll 4
         for (int j = lane; j < c; j += 32) {
           const cplx<T> x = ldcg(&xp[j]), y = ldcg(&xq[j]);
           const cplx<T> uy = cmul<T>(mk<T>(ur, ui), y);
@@ -507,6 +509,7 @@ __global__ void __launch_bounds__(256) onesided_jacobi_kernel(cplx<T>* X, int r,
         }
         cplx<T>* tp = Ut + (size_t)p * r;
         cplx<T>* tq = Ut + (size_t)q * r;
+#pragma unroll 4
         for (int j = lane; j < r; j += 32) {
           const cplx<T> x = ldcg(&tp[j]), y = ldcg(&tq[j]);
           const cplx<T> uy = cmul<T>(mk<T>(ur, -ui), y);
@@ -595,21 +598,25 @@ __global__ void conj_transpose_kernel(const cplx<T>* __restrict__ in, int r, int
 // ---------------------------------------------------------------------------
 constexpr int JB = 16;           // rows per block
 constexpr int JP = 2 * JB;       // rows per pair
-constexpr int JCW = 256;         // columns per Gram / apply work item
+constexpr int JCW = 512;         // columns per Gram / apply work item
 
 
-// In-CTA cyclic Jacobi of the pair's 2JB x 2JB Gram, always in FP64 (the
-// matrix is tiny; FP64 keeps the accumulated rotation J unitary to ~1e-16 so
-// that no rounding drift builds up over the many rounds that reuse U).
-__device__ void bj_inner_eig(double2* Gs /*JP x JP, ld JP+1*/, double2* Vs /*JP x JP, ld JP+1*/, double tol,
-                             int max_sweeps) {
+// In-CTA cyclic Jacobi of the pair's 2JB x 2JB Gram in the working precision
+// TI (FP64 arithmetic runs at 1/64 of the FP32 rate on this part, so nothing
+// here is promoted). The tolerance is set at the rounding level of TI and the
+// sweep count is capped, because J is re-derived in every outer round and an
+// inexact inner solve only costs outer sweeps. The rounding drift of the
+// accumulated rotations is removed afterwards by bj_polish_unitary.
+template <typename TI>
+__device__ void bj_inner_eig(cplx<TI>* Gs /*JP x JP, ld JP+1*/, cplx<TI>* Vs /*JP x JP, ld JP+1*/, double tol,
+                             double floor_abs, int max_sweeps) {
   constexpr int LD = JP + 1;
-  __shared__ double rc[JP / 2], rs[JP / 2], rur[JP / 2], rui[JP / 2];
+  __shared__ TI rc[JP / 2], rs[JP / 2], rur[JP / 2], rui[JP / 2];
   __shared__ int s_act;
   const int tid = threadIdx.x;
   for (int e = tid; e < JP * JP; e += blockDim.x) {
     const int i = e / JP, j = e % JP;
-    Vs[i * LD + j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+    Vs[i * LD + j] = mk<TI>(i == j ? TI(1) : TI(0), TI(0));
   }
   __syncthreads();
   for (int sw = 0; sw < max_sweeps; ++sw) {
@@ -619,51 +626,51 @@ __device__ void bj_inner_eig(double2* Gs /*JP x JP, ld JP+1*/, double2* Vs /*JP 
       if (tid < JP / 2) {
         int p = rr_player(tid, rd, JP), q = rr_player(JP - 1 - tid, rd, JP);
         if (p > q) { int t_ = p; p = q; q = t_; }
-        const double a_ = Gs[p * LD + p].x, b_ = Gs[q * LD + q].x;
-        const double2 g = Gs[p * LD + q];
-        const double ag = hypot(g.x, g.y);
-        double c_ = 1.0, s_ = 0.0, ur = 1.0, ui = 0.0;
-        if (ag > tol * sqrt(fabs(a_ * b_)) && ag > 0.0) {
-          const double zeta = (b_ - a_) / (2.0 * ag);
-          double t;
-          if (fabs(zeta) > 1e16) t = 0.5 / zeta;
-          else t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          c_ = 1.0 / sqrt(1.0 + t * t);
+        const TI a_ = Gs[p * LD + p].x, b_ = Gs[q * LD + q].x;
+        const TI gx = Gs[p * LD + q].x, gy = Gs[p * LD + q].y;
+        const TI ag = hypot(gx, gy);
+        TI c_ = TI(1), s_ = TI(0), ur = TI(1), ui = TI(0);
+        if ((double)ag > fmax(tol * sqrt(fabs((double)a_ * (double)b_)), floor_abs) && ag > TI(0)) {
+          const TI zeta = (b_ - a_) / (TI(2) * ag);
+          TI t;
+          if (fabs(zeta) > TI(1) / eps_of<TI>::value) t = TI(0.5) / zeta;
+          else t = (zeta >= TI(0) ? TI(1) : TI(-1)) / (fabs(zeta) + sqrt(TI(1) + zeta * zeta));
+          c_ = TI(1) / sqrt(TI(1) + t * t);
           s_ = t * c_;
-          ur = g.x / ag; ui = g.y / ag;
-          if (s_ != 0.0) atomicAdd(&s_act, 1);
+          ur = gx / ag; ui = gy / ag;
+          if (s_ != TI(0)) atomicAdd(&s_act, 1);
         }
         rc[tid] = c_; rs[tid] = s_; rur[tid] = ur; rui[tid] = ui;
       }
       __syncthreads();
       for (int e = tid; e < 2 * JP * (JP / 2); e += blockDim.x) {
         const int pi = e % (JP / 2), row = e / (JP / 2);
-        const double s_ = rs[pi];
-        if (s_ == 0.0) continue;
+        const TI s_ = rs[pi];
+        if (s_ == TI(0)) continue;
         int p = rr_player(pi, rd, JP), q = rr_player(JP - 1 - pi, rd, JP);
         if (p > q) { int t_ = p; p = q; q = t_; }
-        double2* R = row < JP ? Gs + row * LD : Vs + (row - JP) * LD;
-        const double c_ = rc[pi];
-        const double2 x = R[p], y = R[q];
-        const double2 uy = cmul<double>(make_double2(rur[pi], -rui[pi]), y);
-        R[p] = make_double2(c_ * x.x - s_ * uy.x, c_ * x.y - s_ * uy.y);
-        R[q] = make_double2(s_ * x.x + c_ * uy.x, s_ * x.y + c_ * uy.y);
+        cplx<TI>* R = row < JP ? Gs + row * LD : Vs + (row - JP) * LD;
+        const TI c_ = rc[pi];
+        const cplx<TI> x = R[p], y = R[q];
+        const cplx<TI> uy = cmul<TI>(mk<TI>(rur[pi], -rui[pi]), y);
+        R[p] = mk<TI>(c_ * x.x - s_ * uy.x, c_ * x.y - s_ * uy.y);
+        R[q] = mk<TI>(s_ * x.x + c_ * uy.x, s_ * x.y + c_ * uy.y);
       }
       __syncthreads();
       for (int e = tid; e < JP * (JP / 2); e += blockDim.x) {
         const int pi = e % (JP / 2), j = e / (JP / 2);
-        const double s_ = rs[pi];
-        if (s_ == 0.0) continue;
+        const TI s_ = rs[pi];
+        if (s_ == TI(0)) continue;
         int p = rr_player(pi, rd, JP), q = rr_player(JP - 1 - pi, rd, JP);
         if (p > q) { int t_ = p; p = q; q = t_; }
-        const double c_ = rc[pi];
-        const double2 x = Gs[p * LD + j], y = Gs[q * LD + j];
-        const double2 uy = cmul<double>(make_double2(rur[pi], rui[pi]), y);
-        double2 np_ = make_double2(c_ * x.x - s_ * uy.x, c_ * x.y - s_ * uy.y);
-        double2 nq_ = make_double2(s_ * x.x + c_ * uy.x, s_ * x.y + c_ * uy.y);
-        if (j == q) np_ = make_double2(0.0, 0.0);
-        if (j == p) { nq_ = make_double2(0.0, 0.0); np_.y = 0.0; }
-        if (j == q) nq_.y = 0.0;
+        const TI c_ = rc[pi];
+        const cplx<TI> x = Gs[p * LD + j], y = Gs[q * LD + j];
+        const cplx<TI> uy = cmul<TI>(mk<TI>(rur[pi], rui[pi]), y);
+        cplx<TI> np_ = mk<TI>(c_ * x.x - s_ * uy.x, c_ * x.y - s_ * uy.y);
+        cplx<TI> nq_ = mk<TI>(s_ * x.x + c_ * uy.x, s_ * x.y + c_ * uy.y);
+        if (j == q) np_ = czero<TI>();
+        if (j == p) { nq_ = czero<TI>(); np_.y = TI(0); }
+        if (j == q) nq_.y = TI(0);
         Gs[p * LD + j] = np_;
         Gs[q * LD + j] = nq_;
       }
@@ -675,15 +682,59 @@ __device__ void bj_inner_eig(double2* Gs /*JP x JP, ld JP+1*/, double2* Vs /*JP 
   }
 }
 
+// One Newton-Schulz step V <- V (3 I - V^H V) / 2 (Higham, Functions of
+// Matrices, Sec. 8.3): for V = Q (I + E) with small Hermitian E the result is
+// unitary to O(|E|^2) + rounding, so the per-pair rotation J carries no
+// accumulated drift into the U of the SVD. S and W are JP x JP scratch
+// (leading dimension JP+1) in shared memory.
+template <typename TI>
+__device__ void bj_polish_unitary(cplx<TI>* Vs, cplx<TI>* S, cplx<TI>* W) {
+  constexpr int LD = JP + 1;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < JP * JP; e += blockDim.x) {      // S = V^H V
+    const int i = e / JP, j = e % JP;
+    cplx<TI> acc = czero<TI>();
+#pragma unroll 8
+    for (int k = 0; k < JP; ++k) cfma<TI>(acc, cconj<TI>(Vs[k * LD + i]), Vs[k * LD + j]);
+    S[i * LD + j] = acc;
+  }
+  __syncthreads();
+  for (int e = tid; e < JP * JP; e += blockDim.x) {      // W = V (3 I - S) / 2
+    const int i = e / JP, j = e % JP;
+    cplx<TI> acc = czero<TI>();
+#pragma unroll 8
+    for (int k = 0; k < JP; ++k) {
+      cplx<TI> m = cscale<TI>(S[k * LD + j], TI(-0.5));
+      if (k == j) m.x += TI(1.5);
+      cfma<TI>(acc, Vs[i * LD + k], m);
+    }
+    W[i * LD + j] = acc;
+  }
+  __syncthreads();
+  for (int e = tid; e < JP * JP; e += blockDim.x) Vs[(e / JP) * LD + (e % JP)] = W[(e / JP) * LD + (e % JP)];
+  __syncthreads();
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, int c, int ldx, cplx<T>* Ut, T* w,
                                                             cplx<T>* Gpart, cplx<T>* Jbuf, int* act_flag, OSCtl* ctl,
                                                             int max_sweeps, T tol_rel, T floor_rel, long long timeout_ns) {
   constexpr int LD = JP + 1;
-  __shared__ double2 Gs[JP * LD];     // phase E: the pair Gram in FP64; phase A: J in T
-  __shared__ double2 Vs[JP * LD];
-  __shared__ cplx<T> tileX[JP][17];
-  cplx<T>* Js = reinterpret_cast<cplx<T>*>(Gs);
+  // one shared buffer, used as the Gram tile in phase G and as the pair Gram
+  // and rotation (Gs, Vs) in phases E and A
+  constexpr int GW = sizeof(T) == 4 ? 128 : 64;          // staged columns in phase G
+  constexpr int TILE_BYTES = JP * (GW + 1) * (int)sizeof(cplx<T>);
+  // Gs, Vs and (FP32 only) the polish scratch W
+  constexpr int GV_BYTES = (sizeof(T) == 4 ? 3 : 2) * JP * LD * (int)sizeof(cplx<T>);
+  constexpr int RED_BYTES = 8 * 16 * 40 * (int)sizeof(T);
+  constexpr int SM_AB = TILE_BYTES > GV_BYTES ? TILE_BYTES : GV_BYTES;
+  constexpr int SM_BYTES = SM_AB > RED_BYTES ? SM_AB : RED_BYTES;
+  __shared__ __align__(16) unsigned char smraw[SM_BYTES];
+  cplx<T>* tile = reinterpret_cast<cplx<T>*>(smraw);
+  cplx<T>* Gs = reinterpret_cast<cplx<T>*>(smraw);     // phase E: the pair Gram; phase A: J^H or J^T
+  cplx<T>* Vs = Gs + JP * LD;
+  __shared__ T s_gmax;
+  cplx<T>* Js = Gs;
   __shared__ T s_floor;
   const int nb = (r + JB - 1) / JB, N = nb + (nb & 1), npairs = N / 2;
   const int nch = (c + JCW - 1) / JCW, nchu = (r + JCW - 1) / JCW;
@@ -714,42 +765,132 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
 
   int sweep = 0;
   bool converged = (r <= 1);
+  bool verify = false;   // this sweep forms full Grams to confirm convergence
   for (; sweep < max_sweeps && !converged; ++sweep) {
     for (int rd = 0; rd < N - 1; ++rd) {
       unsigned long long tph = (blockIdx.x == 0 && tid == 0) ? global_timer_ns() : 0ull;
       // ---- phase G: partial Grams of each pair over column chunks ---------
+      // Sweep 0 forms the full 2JB x 2JB Gram. From sweep 1 on every block's
+      // own rows are mutually orthogonal (each round orthogonalises all rows
+      // of a pair, and a block's rows change only when it is paired), so only
+      // the JB x JB cross block X_P X_Q^H and the row norms are formed; the
+      // diagonal blocks are taken as diagonal. The chunk is staged GW columns
+      // at a time with every load in flight before the first store.
+      const bool full_gram = (sweep == 0) || verify;
       for (long item = blockIdx.x; item < (long)npairs * nch; item += nblk) {
         const int pi = (int)(item / nch), ch = (int)(item % nch);
         int P = rr_player(pi, rd, N), Q = rr_player(N - 1 - pi, rd, N);
         if (P > Q) { int t_ = P; P = Q; Q = t_; }
         if (Q >= nb) continue;
-        // thread (ti, tj) owns G[2ti..2ti+1][2tj..2tj+1]; 16 x 16 threads
+        // full: thread (ti, tj) owns G[ti + 16a][tj + 16b];
+        // cross: k-slice g = tid / 16 (k = g, g + 16, ...), member m = tid % 16
+        // owns C[4 mi + i][4 mj + j], mi = m / 4, mj = m % 4, and the norms of
+        // rows 4 mi + i (mj == 0) and JB + 4 mj + j (mi == 0)
         const int ti = tid >> 4, tj = tid & 15;
-        cplx<T> acc[2][2] = {{czero<T>(), czero<T>()}, {czero<T>(), czero<T>()}};
+        const int mi = (tid & 15) >> 2, mj = tid & 3;
+        cplx<T> acc[4][4];
+        T nrmP[4], nrmQ[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          nrmP[i] = T(0);
+          nrmQ[i] = T(0);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = czero<T>();
+        }
         const int c0 = ch * JCW, c1 = min(c, c0 + JCW);
-        for (int k0 = c0; k0 < c1; k0 += 16) {
-          for (int e = tid; e < JP * 16; e += blockDim.x) {
-            const int i = e >> 4, k = e & 15;
-            const int row = (i < JB ? P * JB + i : Q * JB + (i - JB));
-            cplx<T> v = czero<T>();
-            if (row < r && k0 + k < c1) v = ldcg(&X[(size_t)row * ldx + k0 + k]);
-            tileX[i][k] = v;
+        for (int k0 = c0; k0 < c1; k0 += GW) {
+          __syncthreads();
+          {
+            constexpr int PER = JP * GW / 256;
+            cplx<T> v[PER];
+#pragma unroll
+            for (int s = 0; s < PER; ++s) {
+              const int e = tid + 256 * s, i = e / GW, k = e % GW;
+              const int row = (i < JB ? P * JB + i : Q * JB + (i - JB));
+              v[s] = (row < r && k0 + k < c1) ? ldcg(&X[(size_t)row * ldx + k0 + k]) : czero<T>();
+            }
+#pragma unroll
+            for (int s = 0; s < PER; ++s) {
+              const int e = tid + 256 * s, i = e / GW, k = e % GW;
+              tile[i * (GW + 1) + k] = v[s];
+            }
           }
           __syncthreads();
+          const int kn = min(GW, c1 - k0);
+          if (full_gram) {
 #pragma unroll 4
-          for (int k = 0; k < 16; ++k) {
-            const cplx<T> a0 = tileX[2 * ti][k], a1 = tileX[2 * ti + 1][k];
-            const cplx<T> b0 = cconj<T>(tileX[2 * tj][k]), b1 = cconj<T>(tileX[2 * tj + 1][k]);
-            cfma<T>(acc[0][0], a0, b0); cfma<T>(acc[0][1], a0, b1);
-            cfma<T>(acc[1][0], a1, b0); cfma<T>(acc[1][1], a1, b1);
+            for (int k = 0; k < kn; ++k) {
+              const cplx<T> a0 = tile[ti * (GW + 1) + k], a1 = tile[(ti + 16) * (GW + 1) + k];
+              const cplx<T> b0 = cconj<T>(tile[tj * (GW + 1) + k]), b1 = cconj<T>(tile[(tj + 16) * (GW + 1) + k]);
+              cfma<T>(acc[0][0], a0, b0); cfma<T>(acc[0][1], a0, b1);
+              cfma<T>(acc[1][0], a1, b0); cfma<T>(acc[1][1], a1, b1);
+            }
+          } else {
+            for (int k = (tid >> 4); k < kn; k += 16) {
+              cplx<T> av[4], bv[4];
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                av[i] = tile[(4 * mi + i) * (GW + 1) + k];
+                bv[i] = tile[(JB + 4 * mj + i) * (GW + 1) + k];
+              }
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                nrmP[i] += av[i].x * av[i].x + av[i].y * av[i].y;
+                nrmQ[i] += bv[i].x * bv[i].x + bv[i].y * bv[i].y;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) cfma<T>(acc[i][j], av[i], cconj<T>(bv[j]));
+              }
+            }
+          }
+        }
+        __syncthreads();
+        cplx<T>* Gp = Gpart + ((size_t)pi * nch + ch) * JP * JP;
+        if (full_gram) {
+#pragma unroll
+          for (int a_ = 0; a_ < 2; ++a_)
+#pragma unroll
+            for (int b_ = 0; b_ < 2; ++b_) stcg(&Gp[(ti + 16 * a_) * JP + tj + 16 * b_], acc[a_][b_]);
+        } else {
+          // reduce the 16 k-slices in a fixed order (deterministic, so the
+          // same input always gives the same factorisation): half-warp pairs
+          // by shuffle, then the 8 warps through shared memory
+          constexpr int NV = 40;                                 // 16 complex + 4 + 4 norms
+          T* red = reinterpret_cast<T*>(smraw);                  // [8][16][NV]
+          T vals[NV];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) { vals[2 * (4 * i + j)] = acc[i][j].x; vals[2 * (4 * i + j) + 1] = acc[i][j].y; }
+            vals[32 + i] = nrmP[i];
+            vals[36 + i] = nrmQ[i];
+          }
+#pragma unroll
+          for (int v = 0; v < NV; ++v) vals[v] += __shfl_xor_sync(0xffffffffu, vals[v], 16);
+          if ((tid & 31) < 16) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) red[((tid >> 5) * 16 + (tid & 15)) * NV + v] = vals[v];
+          }
+          __syncthreads();
+          for (int e = tid; e < JP * JP; e += blockDim.x) {
+            const int i = e / JP, j = e % JP;
+            cplx<T> v = czero<T>();
+            if ((i < JB) != (j < JB)) {
+              const bool upper = i < JB;
+              const int pi_ = upper ? i : j, qj = upper ? j - JB : i - JB;
+              const int m = (pi_ >> 2) * 4 + (qj >> 2), o = 2 * (4 * (pi_ & 3) + (qj & 3));
+              T sr = T(0), si = T(0);
+              for (int w = 0; w < 8; ++w) { sr += red[(w * 16 + m) * NV + o]; si += red[(w * 16 + m) * NV + o + 1]; }
+              v = mk<T>(sr, upper ? si : -si);
+            } else if (i == j) {
+              T s = T(0);
+              if (i < JB) { const int m = (i >> 2) * 4; for (int w = 0; w < 8; ++w) s += red[(w * 16 + m) * NV + 32 + (i & 3)]; }
+              else { const int m = (i - JB) >> 2; for (int w = 0; w < 8; ++w) s += red[(w * 16 + m) * NV + 36 + ((i - JB) & 3)]; }
+              v = mk<T>(s, T(0));
+            }
+            stcg(&Gp[e], v);
           }
           __syncthreads();
         }
-        cplx<T>* Gp = Gpart + ((size_t)pi * nch + ch) * JP * JP;
-#pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-          for (int b = 0; b < 2; ++b) stcg(&Gp[(2 * ti + a) * JP + 2 * tj + b], acc[a][b]);
       }
       if (!grid_barrier(&ctl->g, nblk, timeout_ns)) return;
       if (blockIdx.x == 0 && tid == 0) { unsigned long long t2 = global_timer_ns(); ctl->phase_ns[0] += t2 - tph; tph = t2; }
@@ -760,17 +901,23 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
         if (Q >= nb) { if (tid == 0) act_flag[pi] = 0; continue; }
         for (int e = tid; e < JP * JP; e += blockDim.x) {
           double sr = 0.0, si = 0.0;
-          for (int ch = 0; ch < nch; ++ch) {
-            const cplx<T> v = ldcg(&Gpart[((size_t)pi * nch + ch) * JP * JP + e]);
-            sr += (double)v.x; si += (double)v.y;
+          const cplx<T>* src = Gpart + (size_t)pi * nch * JP * JP + e;
+          for (int ch0 = 0; ch0 < nch; ch0 += 8) {   // up to eight loads in flight
+            cplx<T> v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = ch0 + u < nch ? ldcg(src + (size_t)(ch0 + u) * JP * JP) : czero<T>();
+#pragma unroll
+            for (int u = 0; u < 8; ++u) { sr += (double)v[u].x; si += (double)v[u].y; }
           }
-          Gs[(e / JP) * LD + (e % JP)] = make_double2(sr, si);
+          Gs[(e / JP) * LD + (e % JP)] = mk<T>((T)sr, (T)si);
         }
         __shared__ int s_need;
         if (tid == 0) s_need = 0;
         __syncthreads();
-        for (int e = tid; e < JB * JB; e += blockDim.x) {
-          const int i = e / JB, j = JB + e % JB;
+        const bool full_e = (sweep == 0) || verify;
+        for (int e = tid; e < (full_e ? JP * JP : JB * JB); e += blockDim.x) {
+          const int i = full_e ? e / JP : e / JB, j = full_e ? e % JP : JB + e % JB;
+          if (i >= j) continue;
           const double aij = hypot(Gs[i * LD + j].x, Gs[i * LD + j].y);
           const double thr = fmax((double)tol_rel * sqrt(fabs(Gs[i * LD + i].x * Gs[j * LD + j].x)), (double)floor_abs);
           if (aij > thr) s_need = 1;
@@ -778,11 +925,17 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
         __syncthreads();
         const int need = s_need;
         if (need) {
-          bj_inner_eig(Gs, Vs, 1e-14, 15);
-          for (int e = tid; e < JP * JP; e += blockDim.x) {
-            const double2 v = Vs[(e / JP) * LD + (e % JP)];
-            stcg(&Jbuf[(size_t)pi * JP * JP + e], mk<T>((T)v.x, (T)v.y));
+          if (tid == 0) {
+            T gm = T(0);
+            for (int i = 0; i < JP; ++i) gm = fmax(gm, Gs[i * LD + i].x);
+            s_gmax = gm;
           }
+          __syncthreads();
+          bj_inner_eig<T>(Gs, Vs, 4.0 * (double)eps_of<T>::value * sqrt((double)JP),
+                          32.0 * (double)eps_of<T>::value * (double)s_gmax, 3);
+          // FP32: remove the rounding drift of J (FP64 rotations keep it at 1e-16)
+          if constexpr (sizeof(T) == 4) bj_polish_unitary<T>(Vs, Gs, Vs + JP * LD);
+          for (int e = tid; e < JP * JP; e += blockDim.x) stcg(&Jbuf[(size_t)pi * JP * JP + e], Vs[(e / JP) * LD + (e % JP)]);
           if (tid == 0) { act_flag[pi] = 1; atomicAdd(&ctl->active[sweep], 1); }
         } else if (tid == 0) {
           act_flag[pi] = 0;
@@ -829,7 +982,12 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
       if (!grid_barrier(&ctl->g, nblk, timeout_ns)) return;
       if (blockIdx.x == 0 && tid == 0) ctl->phase_ns[2] += global_timer_ns() - tph;
     }
-    if (atomicAdd(&ctl->active[sweep], 0) == 0) converged = true;
+    // a quiet sweep ends the solve only if it formed full Grams (sweep 0 or a
+    // verification sweep); a quiet cross-only sweep triggers a verification
+    const bool quiet = atomicAdd(&ctl->active[sweep], 0) == 0;
+    const bool was_full = (sweep == 0) || verify;
+    if (quiet && was_full) converged = true;
+    verify = quiet && !was_full;
   }
   for (long i = gwarp; i < r; i += nwarps) {
     T s = T(0);

@@ -510,6 +510,75 @@ static int trace_t(mpo_ctx* h, double* tr) {
   return MPO_OK;
 }
 
+// ---------------------------------------------------------- P(x), sampling --
+// Output probabilities P(x) = <<X|rho>> with X = (d+1) x (Sec. 3.4) of S bit
+// strings, or S samples drawn by sequential conditionals (Sec. 3.4) from the
+// caller's uniforms. Scratch is allocated per call (a diagnostic path).
+template <typename T>
+static int chain_t(mpo_ctx* h, int S, const double* uniforms, unsigned char* bits, double* P) {
+  const int n = h->n, cm = h->chi_max;
+  const bool sample = uniforms != nullptr;
+  std::vector<void*> owned;
+  auto dalloc = [&](size_t bytes) -> void* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, std::max<size_t>(bytes, 256)) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    owned.push_back(p);
+    return p;
+  };
+  auto release = [&]() { for (void* p : owned) cudaFree(p); owned.clear(); };
+  cplx<T>* L = (cplx<T>*)dalloc(sizeof(cplx<T>) * (size_t)S * cm);
+  cplx<T>* L2 = (cplx<T>*)dalloc(sizeof(cplx<T>) * (size_t)S * cm);
+  cplx<T>* t0 = (cplx<T>*)dalloc(sizeof(cplx<T>) * (size_t)S * cm);
+  cplx<T>* t1 = (cplx<T>*)dalloc(sizeof(cplx<T>) * (size_t)S * cm);
+  double* ls = (double*)dalloc(sizeof(double) * S);
+  unsigned char* dbits = (unsigned char*)dalloc((size_t)S * n);
+  double* du = sample ? (double*)dalloc(sizeof(double) * (size_t)S * n) : nullptr;
+  double2* R = sample ? (double2*)dalloc(sizeof(double2) * (size_t)(n + 1) * (cm + 1)) : nullptr;
+  if (!L || !L2 || !t0 || !t1 || !ls || !dbits || (sample && (!du || !R))) { release(); return fail(h, MPO_ERR_OOM, "chain scratch"); }
+  auto ck = [&](cudaError_t e) -> bool { if (e != cudaSuccess) { release(); fail(h, MPO_ERR_CUDA, cudaGetErrorString(e)); return false; } return true; };
+  if (!ck(cudaMemsetAsync(ls, 0, sizeof(double) * S, h->st))) return MPO_ERR_CUDA;
+  if (sample) {
+    if (!ck(cudaMemcpyAsync(du, uniforms, sizeof(double) * (size_t)S * n, cudaMemcpyHostToDevice, h->st))) return MPO_ERR_CUDA;
+    // right environments R_k (k = n .. 0), R_n = (1)
+    const double2 one = make_double2(1.0, 0.0);
+    if (!ck(cudaMemcpyAsync(R + (size_t)n * (cm + 1), &one, sizeof(double2), cudaMemcpyHostToDevice, h->st))) return MPO_ERR_CUDA;
+    for (int k = n - 1; k >= 0; --k) {
+      trace_right_kernel<T><<<(h->chi[k] + 127) / 128, 128, 0, h->st>>>(S_<T>(h, k), h->chi[k], h->chi[k + 1],
+                                                                      R + (size_t)(k + 1) * (cm + 1), R + (size_t)k * (cm + 1));
+      if (!ck(cudaGetLastError())) return MPO_ERR_CUDA;
+    }
+  } else {
+    if (!ck(cudaMemcpyAsync(dbits, bits, (size_t)S * n, cudaMemcpyHostToDevice, h->st))) return MPO_ERR_CUDA;
+  }
+  {  // L = 1 for every string (left bond dimension 1)
+    std::vector<cplx<T>> ones(S, mk<T>(T(1), T(0)));
+    if (!ck(cudaMemcpyAsync(L, ones.data(), sizeof(cplx<T>) * S, cudaMemcpyHostToDevice, h->st))) return MPO_ERR_CUDA;
+    if (!ck(cudaStreamSynchronize(h->st))) return MPO_ERR_CUDA;
+  }
+  for (int k = 0; k < n; ++k) {
+    const int cl = h->chi[k], cr = h->chi[k + 1];
+    const cplx<T>* A = S_<T>(h, k);
+    if (!ck(cgemm<T>(h->st, S, cr, cl, L, cl, 0, A, 4 * cr, 0, t0, cr))) return MPO_ERR_CUDA;            // I = 0
+    if (!ck(cgemm<T>(h->st, S, cr, cl, L, cl, 0, A + 3 * (size_t)cr, 4 * cr, 0, t1, cr))) return MPO_ERR_CUDA; // I = 3
+    chain_select_kernel<T><<<(S * 32 + 255) / 256, 256, 0, h->st>>>(t0, t1, S, cr, sample ? R + (size_t)(k + 1) * (cm + 1) : nullptr,
+                                                                   du, dbits, n, k, L2, ls);
+    if (!ck(cudaGetLastError())) return MPO_ERR_CUDA;
+    std::swap(L, L2);
+  }
+  std::vector<cplx<T>> fin(S);
+  std::vector<double> hls(S);
+  double ln = 0.0;
+  if (!ck(cudaMemcpyAsync(fin.data(), L, sizeof(cplx<T>) * S, cudaMemcpyDeviceToHost, h->st))) return MPO_ERR_CUDA;
+  if (!ck(cudaMemcpyAsync(hls.data(), ls, sizeof(double) * S, cudaMemcpyDeviceToHost, h->st))) return MPO_ERR_CUDA;
+  if (!ck(cudaMemcpyAsync(&ln, h->scal, sizeof(double), cudaMemcpyDeviceToHost, h->st))) return MPO_ERR_CUDA;
+  if (sample && !ck(cudaMemcpyAsync(bits, dbits, (size_t)S * n, cudaMemcpyDeviceToHost, h->st))) return MPO_ERR_CUDA;
+  if (!ck(cudaStreamSynchronize(h->st))) return MPO_ERR_CUDA;
+  if (P)
+    for (int s = 0; s < S; ++s) P[s] = (double)fin[s].x * std::exp(hls[s] + ln);
+  release();
+  return MPO_OK;
+}
+
 // ================================================================ C ABI ====
 extern "C" {
 
@@ -768,6 +837,24 @@ int mpo_centre(mpo_handle h, int* c) {
 }
 
 size_t mpo_device_bytes(mpo_handle h) { return h ? h->bytes : 0; }
+
+int mpo_probability(mpo_handle h, int n_strings, const unsigned char* bits, double* P) {
+  GUARD(h);
+  if (n_strings < 1 || !bits || !P) return fail(h, MPO_ERR_ARG, "mpo_probability: bad arguments");
+  for (size_t i = 0; i < (size_t)n_strings * h->n; ++i)
+    if (bits[i] > 1) return fail(h, MPO_ERR_ARG, "mpo_probability: bits must be 0 or 1");
+  return h->prec == MPO_FP64 ? chain_t<double>(h, n_strings, nullptr, const_cast<unsigned char*>(bits), P)
+                             : chain_t<float>(h, n_strings, nullptr, const_cast<unsigned char*>(bits), P);
+}
+
+int mpo_sample(mpo_handle h, int n_samples, const double* uniforms, unsigned char* bits, double* P) {
+  GUARD(h);
+  if (n_samples < 1 || !uniforms || !bits) return fail(h, MPO_ERR_ARG, "mpo_sample: bad arguments");
+  for (size_t i = 0; i < (size_t)n_samples * h->n; ++i)
+    if (!(uniforms[i] >= 0.0 && uniforms[i] < 1.0)) return fail(h, MPO_ERR_ARG, "mpo_sample: uniforms must lie in [0, 1)");
+  return h->prec == MPO_FP64 ? chain_t<double>(h, n_samples, uniforms, bits, P)
+                             : chain_t<float>(h, n_samples, uniforms, bits, P);
+}
 
 int mpo_profile(mpo_handle h, int enable) {
   GUARD(h);

@@ -89,6 +89,7 @@ __global__ void trace_step_kernel(const cplx<T>* __restrict__ A, int chiL, int c
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= chiR) return;
   double re = 0.0, im = 0.0;
+#pragma unroll 4
   for (int a = 0; a < chiL; ++a) {
     const cplx<T> x0 = A[(size_t)(4 * a + 0) * chiR + c];
     const cplx<T> x3 = A[(size_t)(4 * a + 3) * chiR + c];
@@ -106,4 +107,78 @@ __global__ void scale_kernel(cplx<T>* __restrict__ x, size_t n, const double* __
   const double f = reciprocal ? 1.0 / *s : *s;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
     x[e] = cscale<T>(x[e], (T)f);
+}
+
+// ---------------------------------------------------------------------------
+// Right trace environments (Sec. 3.4): R_k[a] = sum_c (A_k[a,0,c] + A_k[a,3,c]) R_{k+1}[c],
+// R_n = (1): the contraction of sites k..n-1 with the vectorised identity.
+// One thread per row a.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void trace_right_kernel(const cplx<T>* __restrict__ A, int chiL, int chiR,
+                                   const double2* __restrict__ rin, double2* __restrict__ rout) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= chiL) return;
+  double re = 0.0, im = 0.0;
+  const cplx<T>* r0 = A + (size_t)(4 * a + 0) * chiR;
+  const cplx<T>* r3 = A + (size_t)(4 * a + 3) * chiR;
+#pragma unroll 4
+  for (int c = 0; c < chiR; ++c) {
+    const double tr = (double)r0[c].x + (double)r3[c].x, ti = (double)r0[c].y + (double)r3[c].y;
+    const double2 v = rin[c];
+    re += tr * v.x - ti * v.y;
+    im += tr * v.y + ti * v.x;
+  }
+  rout[a] = make_double2(re, im);
+}
+
+// ---------------------------------------------------------------------------
+// One site of the probability / sampling chain for S strings at once.
+// t0 = L A_k[:,0,:] and t1 = L A_k[:,3,:] (S x chiR each, computed by GEMM)
+// hold the two continuations x_k = 0, 1 (I = (d+1) x, Sec. 3.4).
+//   sampling (uniforms != null): p_x = Re(t_x . R_{k+1}) is proportional to
+//     the marginal of the first k bits (Sec. 3.4, sequential conditionals);
+//     x_k = 0 if u < p0 / (p0 + p1) else 1 (decided in FP64);
+//   probability (bits given): x_k = bits[s * n + k].
+// The chosen row is rescaled by its largest |entry| and the log of that
+// factor is added to logscale[s], so long chains neither underflow nor
+// overflow. One warp per string.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void chain_select_kernel(const cplx<T>* __restrict__ t0, const cplx<T>* __restrict__ t1, int S, int chiR,
+                                    const double2* __restrict__ Rnext, const double* __restrict__ uniforms,
+                                    unsigned char* __restrict__ bits, int n, int k, cplx<T>* __restrict__ Lout,
+                                    double* __restrict__ logscale) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= S) return;
+  const cplx<T>* a0 = t0 + (size_t)warp * chiR;
+  const cplx<T>* a1 = t1 + (size_t)warp * chiR;
+  int x;
+  if (uniforms) {
+    double p0 = 0.0, p1 = 0.0;
+    for (int c = lane; c < chiR; c += 32) {
+      const double2 r = Rnext[c];
+      p0 += (double)a0[c].x * r.x - (double)a0[c].y * r.y;
+      p1 += (double)a1[c].x * r.x - (double)a1[c].y * r.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      p0 += __shfl_xor_sync(0xffffffffu, p0, o);
+      p1 += __shfl_xor_sync(0xffffffffu, p1, o);
+    }
+    p0 = p0 > 0.0 ? p0 : 0.0;   // truncation can leave tiny negative marginals
+    p1 = p1 > 0.0 ? p1 : 0.0;
+    const double u = uniforms[(size_t)warp * n + k];
+    x = (p0 + p1 > 0.0 && u < p0 / (p0 + p1)) ? 0 : 1;
+    if (p0 + p1 <= 0.0) x = 0;
+    if (lane == 0) bits[(size_t)warp * n + k] = (unsigned char)x;
+  } else {
+    x = bits[(size_t)warp * n + k] ? 1 : 0;
+  }
+  const cplx<T>* src = x ? a1 : a0;
+  double mx = 0.0;
+  for (int c = lane; c < chiR; c += 32) mx = fmax(mx, fmax(fabs((double)src[c].x), fabs((double)src[c].y)));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const double f = mx > 0.0 ? 1.0 / mx : 1.0;
+  for (int c = lane; c < chiR; c += 32) Lout[(size_t)warp * chiR + c] = cscale<T>(src[c], (T)f);
+  if (lane == 0 && mx > 0.0) logscale[warp] += log(mx);
 }

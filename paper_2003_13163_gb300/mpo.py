@@ -20,7 +20,8 @@ ERRORS = {0: "MPO_OK", -1: "MPO_ERR_ARG", -2: "MPO_ERR_CUDA", -3: "MPO_ERR_OOM",
 EXPORTS = ["mpo_default_opts", "mpo_init", "mpo_apply_layer", "mpo_apply_gate", "mpo_apply_superop", "mpo_sweep",
            "mpo_entropy", "mpo_schmidt", "mpo_bond_dims", "mpo_get_site", "mpo_to_dense", "mpo_centre",
            "mpo_device_bytes", "mpo_free", "mpo_last_error", "mpo_eigh", "mpo_svd", "mpo_version",
-           "mpo_profile", "mpo_profile_read", "mpo_profile_sweeps", "mpo_profile_phases", "mpo_svd_static"]
+           "mpo_profile", "mpo_profile_read", "mpo_profile_sweeps", "mpo_profile_phases", "mpo_svd_static",
+           "mpo_probability", "mpo_sample"]
 
 
 class MPOError(RuntimeError):
@@ -73,6 +74,8 @@ def load_library(path: str | None = None):
         "mpo_profile_sweeps": (ctypes.c_longlong, [P]),
         "mpo_profile_phases": (I, [P, DP]),
         "mpo_svd_static": (I, [I, I, P, P, P, I, I, P]),
+        "mpo_probability": (I, [P, I, P, P]),
+        "mpo_sample": (I, [P, I, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -190,6 +193,24 @@ class MPO:
         out = np.empty((4,) * self.n, dtype=np.complex128)
         self._check(self._lib.mpo_to_dense(self.h, _ptr(out)))
         return out
+
+    def probability(self, bits) -> np.ndarray:
+        """P(x) = <<X|rho>> (Sec. 3.4) of bit strings bits: (S, n) of 0/1."""
+        bits = np.ascontiguousarray(bits, dtype=np.uint8)
+        if bits.ndim == 1:
+            bits = bits[None, :]
+        P = np.empty(bits.shape[0])
+        self._check(self._lib.mpo_probability(self.h, bits.shape[0], _ptr(bits), _ptr(P)))
+        return P
+
+    def sample(self, uniforms) -> tuple:
+        """Samples by sequential conditionals (Sec. 3.4) from caller uniforms
+        (S, n) in [0, 1). Returns (bits (S, n) uint8, P(bits) (S,))."""
+        u = np.ascontiguousarray(uniforms, dtype=np.float64)
+        bits = np.empty(u.shape, dtype=np.uint8)
+        P = np.empty(u.shape[0])
+        self._check(self._lib.mpo_sample(self.h, u.shape[0], _ptr(u), _ptr(bits), _ptr(P)))
+        return bits, P
 
     def centre(self) -> int:
         c = ctypes.c_int()

@@ -74,8 +74,9 @@ def test_onesided_svd_fp64_matches_lapack(M, r, c, decay):
 
 @pytest.mark.parametrize("prec,r,c", [("fp64", 40, 100), ("fp64", 300, 512), ("fp32", 33, 64), ("fp32", 520, 1024)])
 def test_block_svd_matches_lapack(M, prec, r, c):
-    """Block one-sided Jacobi: singular values to the Gram-level accuracy
-    (absolute ~ sqrt(eps c) sigma_max), orthonormal U, exact reconstruction."""
+    """Block one-sided Jacobi: singular values to the level the pair Grams
+    resolve (absolute ~ sqrt(16 eps sqrt(c)) sigma_max for the smallest ones,
+    the stopping floor), orthonormal U, exact reconstruction."""
     import torch
     k = min(r, c)
     U = np.linalg.qr(random_complex((r, k), seed=r))[0]
@@ -89,9 +90,11 @@ def test_block_svd_matches_lapack(M, prec, r, c):
     w, Ut, Xo = (w.cpu().numpy().astype(np.float64), Ut.cpu().numpy().astype(np.complex128),
                  Xt.cpu().numpy().astype(np.complex128))
     sv = np.sqrt(np.sort(np.maximum(w, 0))[::-1])[:k]
-    np.testing.assert_allclose(sv, np.linalg.svd(X, compute_uv=False), atol=50 * eps * np.sqrt(c))
+    ref = np.linalg.svd(X, compute_uv=False)
+    np.testing.assert_allclose(sv, ref, atol=np.sqrt(16 * eps * np.sqrt(c)) * ref[0])
+    np.testing.assert_allclose(sv[:k // 4], ref[:k // 4], rtol=100 * eps * np.sqrt(c))
     Um = Ut.T
-    np.testing.assert_allclose(Um.conj().T @ Um, np.eye(r), atol=50 * eps * np.sqrt(r))
+    np.testing.assert_allclose(Um.conj().T @ Um, np.eye(r), atol=200 * eps * np.sqrt(r))
     np.testing.assert_allclose(Um @ Xo, X, atol=50 * eps * np.sqrt(c))
     G = Xo @ Xo.conj().T
     assert np.abs(G - np.diag(np.diag(G))).max() < 50 * eps * np.sqrt(c)
@@ -284,3 +287,25 @@ def test_bad_arguments(M):
     with pytest.raises(M.MPOError) as e:
         m._check(m._lib.mpo_apply_gate(m.h, 9, None, 0.0))
     assert e.value.code == -1
+
+
+# ------------------------------------------------- probabilities, sampling --
+def test_probabilities_and_samples_match_oracle(M):
+    """Sec. 3.4 on the GPU: P(x) of every string and sequential-conditional
+    samples (same uniforms) against the dense oracle."""
+    from oracle import sampling
+    from paper_2003_13163_gb300.circuits import sampling_uniforms
+    import itertools
+    for n, chi, p, D in [(6, 64, 0.03, 4), (8, 8, 0.05, 5)]:
+        c = random_circuit(n, D, p, seed=n + chi)
+        d = dense.run(c, chi, 1e-12)
+        _, _, _, m = run_gpu(M, c, chi, cutoff=1e-12)
+        allbits = np.array(list(itertools.product((0, 1), repeat=n)), dtype=np.uint8)
+        P = m.probability(allbits)
+        np.testing.assert_allclose(P, sampling.all_probabilities(d.final), atol=1e-12)
+        np.testing.assert_allclose(P.sum(), d.trace[-1], atol=1e-12)
+        u = sampling_uniforms(400, n, seed=5)
+        bits, Ps = m.sample(u)
+        ref = sampling.sample(d.final, u)
+        assert np.array_equal(bits, ref)
+        np.testing.assert_allclose(Ps, sampling.probabilities(d.final, ref), atol=1e-12)
