@@ -578,6 +578,41 @@ __global__ void conj_transpose_kernel(const cplx<T>* __restrict__ in, int r, int
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// TMA bulk-copy staging (cp.async.bulk, global -> shared) with mbarrier
+// completion. Every wait is bounded; on expiry the error word is set.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_addr(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n"
+               :: "r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+
+// Wait for phase `parity` of bar; false if the wait exceeded timeout_ns.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long timeout_ns) {
+  unsigned long long t0 = 0;
+  for (long it = 0;; ++it) {
+    unsigned ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    if (ok) return true;
+    if (it == 0) t0 = global_timer_ns();
+    else if ((it & 255) == 0 && (long long)(global_timer_ns() - t0) > timeout_ns) return false;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Block one-sided Jacobi SVD (row blocks of JB rows; a pair holds 2 JB rows).
 // Same contract as onesided_jacobi_kernel: X (r x c) <- U^H X with rows
@@ -607,48 +642,58 @@ constexpr int JCW = 512;         // columns per Gram / apply work item
 // sweep count is capped, because J is re-derived in every outer round and an
 // inexact inner solve only costs outer sweeps. The rounding drift of the
 // accumulated rotations is removed afterwards by bj_polish_unitary.
+template <typename TI> __device__ __forceinline__ TI rsqrt_fast(TI x);
+template <> __device__ __forceinline__ float rsqrt_fast<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double rsqrt_fast<double>(double x) { return rsqrt(x); }
+
 template <typename TI>
 __device__ void bj_inner_eig(cplx<TI>* Gs /*JP x JP, ld JP+1*/, cplx<TI>* Vs /*JP x JP, ld JP+1*/, double tol,
                              double floor_abs, int max_sweeps) {
   constexpr int LD = JP + 1;
   __shared__ TI rc[JP / 2], rs[JP / 2], rur[JP / 2], rui[JP / 2];
-  __shared__ int s_act;
+  __shared__ int rp[JP / 2], rq[JP / 2];
   const int tid = threadIdx.x;
   for (int e = tid; e < JP * JP; e += blockDim.x) {
     const int i = e / JP, j = e % JP;
     Vs[i * LD + j] = mk<TI>(i == j ? TI(1) : TI(0), TI(0));
   }
   __syncthreads();
+  const TI tol2 = (TI)(tol * tol), flo2 = (TI)(floor_abs * floor_abs);
   for (int sw = 0; sw < max_sweeps; ++sw) {
-    if (tid == 0) s_act = 0;
-    __syncthreads();
+    int any = 0;
     for (int rd = 0; rd < JP - 1; ++rd) {
+      // rotation table of the round (the pairs and their parameters); the
+      // square-root-free test |g|^2 > max(tol^2 a b, floor^2) decides a skip
+      int act = 0;
       if (tid < JP / 2) {
         int p = rr_player(tid, rd, JP), q = rr_player(JP - 1 - tid, rd, JP);
         if (p > q) { int t_ = p; p = q; q = t_; }
+        rp[tid] = p; rq[tid] = q;
         const TI a_ = Gs[p * LD + p].x, b_ = Gs[q * LD + q].x;
         const TI gx = Gs[p * LD + q].x, gy = Gs[p * LD + q].y;
-        const TI ag = hypot(gx, gy);
+        const TI g2 = gx * gx + gy * gy;
         TI c_ = TI(1), s_ = TI(0), ur = TI(1), ui = TI(0);
-        if ((double)ag > fmax(tol * sqrt(fabs((double)a_ * (double)b_)), floor_abs) && ag > TI(0)) {
-          const TI zeta = (b_ - a_) / (TI(2) * ag);
+        if (g2 > fmax(tol2 * fabs(a_ * b_), flo2) && g2 > TI(0)) {
+          const TI inv = rsqrt_fast<TI>(g2), ag = g2 * inv;          // 1/|g|, |g|
+          const TI zeta = (b_ - a_) * TI(0.5) * inv;
           TI t;
           if (fabs(zeta) > TI(1) / eps_of<TI>::value) t = TI(0.5) / zeta;
           else t = (zeta >= TI(0) ? TI(1) : TI(-1)) / (fabs(zeta) + sqrt(TI(1) + zeta * zeta));
-          c_ = TI(1) / sqrt(TI(1) + t * t);
+          c_ = rsqrt_fast<TI>(TI(1) + t * t);
           s_ = t * c_;
-          ur = gx / ag; ui = gy / ag;
-          if (s_ != TI(0)) atomicAdd(&s_act, 1);
+          ur = gx * inv; ui = gy * inv;
+          (void)ag;
+          act = (s_ != TI(0));
         }
-        rc[tid] = c_; rs[tid] = s_; rur[tid] = ur; rui[tid] = ui;
+        rc[tid] = c_; rs[tid] = act ? s_ : TI(0); rur[tid] = ur; rui[tid] = ui;
       }
-      __syncthreads();
+      if (!__syncthreads_or(act)) continue;   // nothing to rotate this round
+      any = 1;
       for (int e = tid; e < 2 * JP * (JP / 2); e += blockDim.x) {
         const int pi = e % (JP / 2), row = e / (JP / 2);
         const TI s_ = rs[pi];
         if (s_ == TI(0)) continue;
-        int p = rr_player(pi, rd, JP), q = rr_player(JP - 1 - pi, rd, JP);
-        if (p > q) { int t_ = p; p = q; q = t_; }
+        const int p = rp[pi], q = rq[pi];
         cplx<TI>* R = row < JP ? Gs + row * LD : Vs + (row - JP) * LD;
         const TI c_ = rc[pi];
         const cplx<TI> x = R[p], y = R[q];
@@ -661,8 +706,7 @@ __device__ void bj_inner_eig(cplx<TI>* Gs /*JP x JP, ld JP+1*/, cplx<TI>* Vs /*J
         const int pi = e % (JP / 2), j = e / (JP / 2);
         const TI s_ = rs[pi];
         if (s_ == TI(0)) continue;
-        int p = rr_player(pi, rd, JP), q = rr_player(JP - 1 - pi, rd, JP);
-        if (p > q) { int t_ = p; p = q; q = t_; }
+        const int p = rp[pi], q = rq[pi];
         const TI c_ = rc[pi];
         const cplx<TI> x = Gs[p * LD + j], y = Gs[q * LD + j];
         const cplx<TI> uy = cmul<TI>(mk<TI>(rur[pi], rui[pi]), y);
@@ -676,9 +720,7 @@ __device__ void bj_inner_eig(cplx<TI>* Gs /*JP x JP, ld JP+1*/, cplx<TI>* Vs /*J
       }
       __syncthreads();
     }
-    const int act = s_act;
-    __syncthreads();
-    if (act == 0) break;
+    if (!any) break;
   }
 }
 
@@ -715,24 +757,37 @@ __device__ void bj_polish_unitary(cplx<TI>* Vs, cplx<TI>* S, cplx<TI>* W) {
   __syncthreads();
 }
 
+template <typename T> struct BJ_GW { static constexpr int value = sizeof(T) == 4 ? 128 : 64; };
+__device__ __forceinline__ bool tid_is_zero() { return threadIdx.x == 0; }
+
+// Dynamic shared memory of block_jacobi_kernel<T>: the larger of two staging
+// tiles, the phase E/A matrices and the cross-block reduction buffer.
+template <typename T>
+constexpr int block_jacobi_smem_bytes() {
+  constexpr int GW = BJ_GW<T>::value;
+  constexpr int TS = GW + 16 / (int)sizeof(cplx<T>);
+  constexpr int TILES = 2 * JP * TS * (int)sizeof(cplx<T>);
+  constexpr int GV = 3 * JP * (JP + 1) * (int)sizeof(cplx<T>);
+  constexpr int RED = 8 * 16 * 40 * (int)sizeof(T);
+  constexpr int M1 = TILES > GV ? TILES : GV;
+  return M1 > RED ? M1 : RED;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, int c, int ldx, cplx<T>* Ut, T* w,
                                                             cplx<T>* Gpart, cplx<T>* Jbuf, int* act_flag, OSCtl* ctl,
                                                             int max_sweeps, T tol_rel, T floor_rel, long long timeout_ns) {
   constexpr int LD = JP + 1;
-  // one shared buffer, used as the Gram tile in phase G and as the pair Gram
-  // and rotation (Gs, Vs) in phases E and A
-  constexpr int GW = sizeof(T) == 4 ? 128 : 64;          // staged columns in phase G
-  constexpr int TILE_BYTES = JP * (GW + 1) * (int)sizeof(cplx<T>);
-  // Gs, Vs and (FP32 only) the polish scratch W
-  constexpr int GV_BYTES = (sizeof(T) == 4 ? 3 : 2) * JP * LD * (int)sizeof(cplx<T>);
-  constexpr int RED_BYTES = 8 * 16 * 40 * (int)sizeof(T);
-  constexpr int SM_AB = TILE_BYTES > GV_BYTES ? TILE_BYTES : GV_BYTES;
-  constexpr int SM_BYTES = SM_AB > RED_BYTES ? SM_AB : RED_BYTES;
-  __shared__ __align__(16) unsigned char smraw[SM_BYTES];
-  cplx<T>* tile = reinterpret_cast<cplx<T>*>(smraw);
+  // Dynamic shared memory (block_jacobi_smem_bytes<T>()): two phase-G tiles
+  // of JP rows x TS columns (double buffer); phases E and A reuse the same
+  // bytes for the pair Gram Gs, the rotation Vs and the polish scratch.
+  constexpr int GW = BJ_GW<T>::value;                    // staged columns in phase G
+  constexpr int TS = GW + 16 / (int)sizeof(cplx<T>);     // padded row stride (elements)
+  extern __shared__ __align__(128) unsigned char smraw[];
+  cplx<T>* tiles[2] = {reinterpret_cast<cplx<T>*>(smraw), reinterpret_cast<cplx<T>*>(smraw) + JP * TS};
   cplx<T>* Gs = reinterpret_cast<cplx<T>*>(smraw);     // phase E: the pair Gram; phase A: J^H or J^T
   cplx<T>* Vs = Gs + JP * LD;
+
   __shared__ T s_gmax;
   cplx<T>* Js = Gs;
   __shared__ T s_floor;
@@ -798,30 +853,37 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
           for (int j = 0; j < 4; ++j) acc[i][j] = czero<T>();
         }
         const int c0 = ch * JCW, c1 = min(c, c0 + JCW);
-        for (int k0 = c0; k0 < c1; k0 += GW) {
-          __syncthreads();
-          {
-            constexpr int PER = JP * GW / 256;
-            cplx<T> v[PER];
+        const int nsub = (c1 - c0 + GW - 1) / GW;
+        // register staging with one sub-chunk of prefetch: the loads of
+        // sub-chunk s+1 are in flight while sub-chunk s is computed
+        constexpr int PER = JP * GW / 256;
+        cplx<T> v[PER];
+        auto load = [&](int s) {
+          const int k0 = c0 + s * GW;
 #pragma unroll
-            for (int s = 0; s < PER; ++s) {
-              const int e = tid + 256 * s, i = e / GW, k = e % GW;
-              const int row = (i < JB ? P * JB + i : Q * JB + (i - JB));
-              v[s] = (row < r && k0 + k < c1) ? ldcg(&X[(size_t)row * ldx + k0 + k]) : czero<T>();
-            }
+          for (int u = 0; u < PER; ++u) {
+            const int e = tid + 256 * u, i = e / GW, k = e % GW;
+            const int row = (i < JB ? P * JB + i : Q * JB + (i - JB));
+            v[u] = (row < r && k0 + k < c1) ? ldcg(&X[(size_t)row * ldx + k0 + k]) : czero<T>();
+          }
+        };
+        __syncthreads();
+        load(0);
+        for (int s = 0; s < nsub; ++s) {
+          cplx<T>* tile = tiles[s & 1];
 #pragma unroll
-            for (int s = 0; s < PER; ++s) {
-              const int e = tid + 256 * s, i = e / GW, k = e % GW;
-              tile[i * (GW + 1) + k] = v[s];
-            }
+          for (int u = 0; u < PER; ++u) {
+            const int e = tid + 256 * u, i = e / GW, k = e % GW;
+            tile[i * TS + k] = v[u];
           }
           __syncthreads();
-          const int kn = min(GW, c1 - k0);
+          if (s + 1 < nsub) load(s + 1);
+          const int kn = min(GW, c1 - (c0 + s * GW));
           if (full_gram) {
 #pragma unroll 4
             for (int k = 0; k < kn; ++k) {
-              const cplx<T> a0 = tile[ti * (GW + 1) + k], a1 = tile[(ti + 16) * (GW + 1) + k];
-              const cplx<T> b0 = cconj<T>(tile[tj * (GW + 1) + k]), b1 = cconj<T>(tile[(tj + 16) * (GW + 1) + k]);
+              const cplx<T> a0 = tile[ti * TS + k], a1 = tile[(ti + 16) * TS + k];
+              const cplx<T> b0 = cconj<T>(tile[tj * TS + k]), b1 = cconj<T>(tile[(tj + 16) * TS + k]);
               cfma<T>(acc[0][0], a0, b0); cfma<T>(acc[0][1], a0, b1);
               cfma<T>(acc[1][0], a1, b0); cfma<T>(acc[1][1], a1, b1);
             }
@@ -830,8 +892,8 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
               cplx<T> av[4], bv[4];
 #pragma unroll
               for (int i = 0; i < 4; ++i) {
-                av[i] = tile[(4 * mi + i) * (GW + 1) + k];
-                bv[i] = tile[(JB + 4 * mj + i) * (GW + 1) + k];
+                av[i] = tile[(4 * mi + i) * TS + k];
+                bv[i] = tile[(JB + 4 * mj + i) * TS + k];
               }
 #pragma unroll
               for (int i = 0; i < 4; ++i) {

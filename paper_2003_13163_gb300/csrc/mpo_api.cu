@@ -239,8 +239,11 @@ template <typename T>
 static cudaError_t launch_block_jacobi(cudaStream_t st, cplx<T>* X, int r, int c, int ldx, cplx<T>* Ut, T* w,
                                       cplx<T>* Gpart, cplx<T>* Jbuf, int* act, OSCtl* ctl, int max_sweeps,
                                       double timeout_s, int num_sms) {
+  const int smem = block_jacobi_smem_bytes<T>();
+  cudaError_t e = cudaFuncSetAttribute(block_jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, block_jacobi_kernel<T>, 256, 0);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, block_jacobi_kernel<T>, 256, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int nb = (r + JB - 1) / JB, npairs = (nb + (nb & 1)) / 2;
@@ -256,7 +259,7 @@ static cudaError_t launch_block_jacobi(cudaStream_t st, cplx<T>* X, int r, int c
   long long timeout_ns = (long long)(timeout_s * 1e9);
   void* args[] = {&X, &r, &c, &ldx, &Ut, &w, &Gpart, &Jbuf, &act, &ctl, &max_sweeps, (void*)&tol_rel,
                   (void*)&floor_rel, &timeout_ns};
-  return cudaLaunchCooperativeKernel((const void*)block_jacobi_kernel<T>, dim3(blocks), dim3(256), args, 0, st);
+  return cudaLaunchCooperativeKernel((const void*)block_jacobi_kernel<T>, dim3(blocks), dim3(256), args, smem, st);
 }
 
 // One-sided Jacobi SVD of X (r x c, rows orthogonalised in place; left factor
@@ -953,6 +956,7 @@ int mpo_to_dense(mpo_handle h, double* rho_vec) {
 
 int mpo_svd(int r, int c, void* X, void* w, void* Ut, mpo_precision prec, int max_sweeps, int block, void* stream) {
   if (r < 1 || c < 1 || !X || !w || !Ut) return MPO_ERR_ARG;
+
   cudaStream_t st = (cudaStream_t)stream;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return MPO_ERR_CUDA;
