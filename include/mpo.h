@@ -81,6 +81,9 @@ typedef struct {
                                < 0 = never]. The block form needs far fewer passes over
                                the matrix but resolves singular values only to about
                                sqrt(eps) * sigma_max relative accuracy per row pair. */
+  int tensor_cores;         /* FP32 only: plain complex products (theta, centre moves) on the
+                               tcgen05 tensor cores with 3 x TF32 split products [0 = on;
+                               < 0 = off, SIMT FP32 instead] */
 } mpo_opts;
 
 /* Fill *o with the defaults. */
@@ -249,6 +252,13 @@ int mpo_svd(int r, int c, void *X, void *w, void *Ut, mpo_precision prec, int ma
  *     status). */
 int mpo_svd_static(int r, int c, void *X, void *w, void *Ut, mpo_precision prec, int max_sweeps,
                    void *cuda_stream);
+
+/* Stand-alone complex GEMM used by the path, exported for tests:
+ * C (M x N) = A (M x K) B (K x N), row-major, interleaved complex, device
+ * pointers. tensor_cores = 1 (FP32 only) runs the tcgen05 kernel with 3 x TF32
+ * split products, 0 the SIMT kernel of the given precision. */
+int mpo_gemm(int M, int N, int K, const void *A, const void *B, void *C, mpo_precision prec, int tensor_cores,
+             void *cuda_stream);
 
 /* Library version string. */
 const char *mpo_version(void);

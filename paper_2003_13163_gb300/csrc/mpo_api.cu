@@ -38,6 +38,7 @@
 #include "common.cuh"
 #include "linalg.cuh"
 #include "mpo_kernels.cuh"
+#include "tcgemm.cuh"
 
 namespace {
 
@@ -47,6 +48,7 @@ struct HostSync {   // pinned read-back of the last select + eigen-solve
   SelectInfo info;
   GridCtl ctl;
   unsigned long long phase_ns[4];
+  int tc_err;
 };
 
 }  // namespace
@@ -77,6 +79,8 @@ struct mpo_ctx {
   void *bj_gpart = nullptr, *bj_j = nullptr;   // block Jacobi workspaces
   int* bj_act = nullptr;
   int block_min_rows = 0;
+  bool tensor_cores = false;       // FP32 plain products on tcgen05
+  int* tc_status = nullptr;        // set by the tensor-core GEMM if a wait timed out
   double* scal = nullptr;          // [0] lognorm, [1] discarded accumulator
   double* dS = nullptr;            // [n-1]
   double* dschmidt = nullptr;      // [(n-1) * chi_max]
@@ -96,14 +100,15 @@ struct mpo_ctx {
   struct Pending { int cls; cudaEvent_t a, b; double flops, bytes; };
   std::vector<Pending> pend;
   std::vector<cudaEvent_t> evpool;
-  double prof_ms[8] = {0}, prof_flops[8] = {0}, prof_bytes[8] = {0};
-  long long prof_n[8] = {0};
+  double prof_ms[16] = {0}, prof_flops[16] = {0}, prof_bytes[16] = {0};
+  long long prof_n[16] = {0};
   long long prof_sweeps = 0;
   double prof_phase_ns[3] = {0, 0, 0};
 };
 
-enum { PK_SVD = 0, PK_GEMM, PK_SUPEROP, PK_SELECT, PK_GATHER, PK_TRANSPOSE, PK_TRACE, PK_NCLASS };
-static const char* kProfNames[PK_NCLASS] = {"svd_jacobi", "cgemm", "superop", "select", "gather", "transpose", "trace"};
+enum { PK_SVD = 0, PK_GEMM, PK_SUPEROP, PK_SELECT, PK_GATHER, PK_TRANSPOSE, PK_TRACE, PK_TCGEMM, PK_NCLASS };
+static const char* kProfNames[PK_NCLASS] = {"svd_jacobi", "cgemm", "superop", "select", "gather", "transpose", "trace",
+                                            "tc_cgemm"};
 
 static cudaEvent_t prof_event(mpo_ctx* h) {
   if (!h->evpool.empty()) { cudaEvent_t e = h->evpool.back(); h->evpool.pop_back(); return e; }
@@ -291,7 +296,9 @@ static int svd_select(mpo_ctx* h, cplx<T>* X, int r, int c, int ldx, int cap, bo
   CK(h, cudaMemcpyAsync(&h->hs->info, h->info, sizeof(SelectInfo), cudaMemcpyDeviceToHost, h->st));
   CK(h, cudaMemcpyAsync(&h->hs->ctl, &h->osctl->g, sizeof(GridCtl), cudaMemcpyDeviceToHost, h->st));
   if (h->prof) CK(h, cudaMemcpyAsync(h->hs->phase_ns, h->osctl->phase_ns, sizeof(h->hs->phase_ns), cudaMemcpyDeviceToHost, h->st));
+  CK(h, cudaMemcpyAsync(&h->hs->tc_err, h->tc_status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
   CK(h, cudaStreamSynchronize(h->st));
+  if (h->hs->tc_err) return fail(h, MPO_ERR_TIMEOUT, "an mbarrier wait timed out in the tensor-core GEMM");
   if (h->prof) for (int i = 0; i < 3; ++i) h->prof_phase_ns[i] += h->hs->phase_ns[i];
   if (h->hs->ctl.err) return fail(h, MPO_ERR_TIMEOUT, "grid barrier wait timed out in the SVD");
   h->last_sweeps = h->hs->ctl.sweeps;
@@ -304,10 +311,35 @@ static int svd_select(mpo_ctx* h, cplx<T>* X, int r, int c, int ldx, int cap, bo
 
 template <typename T> static cplx<T>* S_(mpo_ctx* h, int k) { return (cplx<T>*)h->site[k]; }
 
+// Plain complex64 products large enough to fill a 128 x 64 tile go to the
+// tensor cores (tcgen05, 3 x TF32); everything else runs on the SIMT kernel.
+static cudaError_t tc_cgemm(cudaStream_t st, int M, int N, int K, const float2* A, int lda, const float2* B, int ldb,
+                            float2* C, int ldc, const double* alpha_dev, double alpha_host, int* status,
+                            double timeout_s) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(tc_cgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tcg::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  dim3 grid((N + tcg::BNC - 1) / tcg::BNC, (M + tcg::BM - 1) / tcg::BM);
+  tc_cgemm_kernel<<<grid, 128, tcg::SMEM_BYTES, st>>>(M, N, K, A, lda, B, ldb, C, ldc, alpha_dev, alpha_host, status,
+                                                        (long long)(timeout_s * 1e9));
+  return cudaGetLastError();
+}
+
+static bool use_tensor_cores(int M, int N, int K) { return M >= 64 && N >= 32 && K >= 16; }
+
 template <typename T>
 static cudaError_t gemm_p(mpo_ctx* h, int M, int N, int K, const cplx<T>* A, int lda, int opA, const cplx<T>* B,
                           int ldb, int opB, cplx<T>* C, int ldc, const double* alpha_dev = nullptr) {
   ProfScope ps(h, PK_GEMM, 8.0 * M * N * K, (double)((size_t)M * K + (size_t)K * N + (size_t)M * N) * sizeof(cplx<T>));
+  if constexpr (std::is_same<T, float>::value) {
+    if (h->tensor_cores && opA == 0 && opB == 0 && use_tensor_cores(M, N, K)) {
+      ps.cls = PK_TCGEMM;
+      return tc_cgemm(h->st, M, N, K, A, lda, B, ldb, C, ldc, alpha_dev, 1.0, h->tc_status, h->opts.barrier_timeout_s);
+    }
+  }
   return cgemm<T>(h->st, M, N, K, A, lda, opA, B, ldb, opB, C, ldc, alpha_dev, 1.0);
 }
 
@@ -593,6 +625,7 @@ void mpo_default_opts(mpo_opts* o) {
   o->smode = MPO_S_ALL_BONDS;
   o->barrier_timeout_s = 5.0;
   o->block_jacobi_min_rows = 0;
+  o->tensor_cores = 0;
 }
 
 const char* mpo_version(void) { return "gb300-mpo 0.1 (sm_103a)"; }
@@ -650,6 +683,7 @@ int mpo_init(mpo_handle* out, int n, int chi_max, mpo_precision prec, void* stre
   const int jac_limit = prec == MPO_FP64 ? 8192 : 16384;   // rotation table must fit shared memory
   if (m > jac_limit) return init_fail(h, MPO_ERR_ARG, "bond dimension too large for the eigen-solver's shared-memory table");
   h->tmp_cap = (size_t)m * chi_max;
+  h->tensor_cores = prec == MPO_FP32 && h->opts.tensor_cores >= 0;
   h->block_min_rows = h->opts.block_jacobi_min_rows < 0 ? 0
                       : (h->opts.block_jacobi_min_rows > 0 ? h->opts.block_jacobi_min_rows : (prec == MPO_FP32 ? 64 : 0));
   const size_t bj_pairs = (size_t)((m + JB - 1) / JB + 1) / 2 + 1;
@@ -688,6 +722,7 @@ int mpo_init(mpo_handle* out, int n, int chi_max, mpo_precision prec, void* stre
   ok = ok && alloc((void**)&h->info, sizeof(SelectInfo));
   ok = ok && alloc((void**)&h->ctl, sizeof(GridCtl));
   ok = ok && alloc((void**)&h->osctl, sizeof(OSCtl));
+  ok = ok && alloc((void**)&h->tc_status, sizeof(int));
   if (h->block_min_rows > 0) {
     ok = ok && alloc(&h->bj_gpart, bj_pairs * bj_nch * JP * JP * h->esz);
     ok = ok && alloc(&h->bj_j, bj_pairs * JP * JP * h->esz);
@@ -713,7 +748,8 @@ int mpo_init(mpo_handle* out, int n, int chi_max, mpo_precision prec, void* stre
         cudaMemcpyAsync(h->site[k], one.data(), h->esz, cudaMemcpyHostToDevice, h->st) != cudaSuccess)
       return init_fail(h, MPO_ERR_CUDA, "initial state upload failed");
   }
-  if (cudaMemsetAsync(h->scal, 0, 4 * sizeof(double), h->st) != cudaSuccess ||
+  if (cudaMemsetAsync(h->tc_status, 0, sizeof(int), h->st) != cudaSuccess ||
+      cudaMemsetAsync(h->scal, 0, 4 * sizeof(double), h->st) != cudaSuccess ||
       cudaMemsetAsync(h->dS, 0, (size_t)(n - 1) * sizeof(double), h->st) != cudaSuccess ||
       cudaStreamSynchronize(h->st) != cudaSuccess)
     return init_fail(h, MPO_ERR_CUDA, "initial state upload failed");
@@ -733,7 +769,7 @@ int mpo_init(mpo_handle* out, int n, int chi_max, mpo_precision prec, void* stre
 void mpo_free(mpo_handle h) {
   if (!h) return;
   for (void* p : h->site) if (p) cudaFree(p);
-  void* ps[] = {h->spare, h->theta, h->theta2, h->osctl, h->bj_gpart, h->bj_j, h->bj_act, h->vecs, h->tmp, h->wv, h->perm, h->lam2, h->Ms, h->dgates,
+  void* ps[] = {h->spare, h->theta, h->theta2, h->osctl, h->tc_status, h->bj_gpart, h->bj_j, h->bj_act, h->vecs, h->tmp, h->wv, h->perm, h->lam2, h->Ms, h->dgates,
                 h->dsup, h->dp, h->info, h->ctl, h->scal, h->dS, h->dschmidt, h->tv0, h->tv1};
   for (void* p : ps) if (p) cudaFree(p);
   if (h->hs) cudaFreeHost(h->hs);
@@ -1074,6 +1110,30 @@ int mpo_svd_static(int r, int c, void* X, void* w, void* Ut, mpo_precision prec,
   if (hc.err) return MPO_ERR_TIMEOUT;
   if (hc.status) return MPO_ERR_NOCONV;
   return MPO_OK;
+}
+
+int mpo_gemm(int M, int N, int K, const void* A, const void* B, void* C, mpo_precision prec, int tensor_cores,
+             void* stream) {
+  if (M < 1 || N < 1 || K < 1 || !A || !B || !C) return MPO_ERR_ARG;
+  if (tensor_cores && prec != MPO_FP32) return MPO_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e;
+  int* status = nullptr;
+  if (tensor_cores) {
+    if (cudaMalloc(&status, sizeof(int)) != cudaSuccess) return MPO_ERR_OOM;
+    cudaMemsetAsync(status, 0, sizeof(int), st);
+    e = tc_cgemm(st, M, N, K, (const float2*)A, K, (const float2*)B, N, (float2*)C, N, nullptr, 1.0, status, 5.0);
+  } else if (prec == MPO_FP64) {
+    e = cgemm<double>(st, M, N, K, (const double2*)A, K, 0, (const double2*)B, N, 0, (double2*)C, N);
+  } else {
+    e = cgemm<float>(st, M, N, K, (const float2*)A, K, 0, (const float2*)B, N, 0, (float2*)C, N);
+  }
+  int hs = 0;
+  if (e == cudaSuccess && status) e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (status) cudaFree(status);
+  if (e != cudaSuccess) { g_last_init_error = cudaGetErrorString(e); return MPO_ERR_CUDA; }
+  return hs ? MPO_ERR_TIMEOUT : MPO_OK;
 }
 
 int mpo_eigh(int m, void* A, void* w, void* V, mpo_precision prec, int max_sweeps, void* stream) {

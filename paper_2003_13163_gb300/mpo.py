@@ -21,7 +21,7 @@ EXPORTS = ["mpo_default_opts", "mpo_init", "mpo_apply_layer", "mpo_apply_gate", 
            "mpo_entropy", "mpo_schmidt", "mpo_bond_dims", "mpo_get_site", "mpo_to_dense", "mpo_centre",
            "mpo_device_bytes", "mpo_free", "mpo_last_error", "mpo_eigh", "mpo_svd", "mpo_version",
            "mpo_profile", "mpo_profile_read", "mpo_profile_sweeps", "mpo_profile_phases", "mpo_svd_static",
-           "mpo_probability", "mpo_sample"]
+           "mpo_probability", "mpo_sample", "mpo_gemm"]
 
 
 class MPOError(RuntimeError):
@@ -33,7 +33,8 @@ class MPOError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("eig_max_sweeps", ctypes.c_int), ("sv_rel_cutoff", ctypes.c_double),
                 ("arena_cap_bytes", ctypes.c_size_t), ("smode", ctypes.c_int),
-                ("barrier_timeout_s", ctypes.c_double), ("block_jacobi_min_rows", ctypes.c_int)]
+                ("barrier_timeout_s", ctypes.c_double), ("block_jacobi_min_rows", ctypes.c_int),
+                ("tensor_cores", ctypes.c_int)]
 
 
 _lib = None
@@ -76,6 +77,7 @@ def load_library(path: str | None = None):
         "mpo_svd_static": (I, [I, I, P, P, P, I, I, P]),
         "mpo_probability": (I, [P, I, P, P]),
         "mpo_sample": (I, [P, I, P, P, P]),
+        "mpo_gemm": (I, [I, I, I, P, P, P, I, I, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -113,7 +115,8 @@ class MPO:
 
     def __init__(self, n: int, chi_max: int, precision: str = "fp64", *, cutoff: float = 0.0,
                  eig_max_sweeps: int = 0, arena_cap_bytes: int = 0, centre_only: bool = False,
-                 barrier_timeout_s: float = 0.0, block_jacobi_min_rows: int = 0, stream=None):
+                 barrier_timeout_s: float = 0.0, block_jacobi_min_rows: int = 0, tensor_cores: bool = True,
+                 stream=None):
         lib = load_library()
         self._lib = lib
         self.n, self.chi_max = n, chi_max
@@ -128,6 +131,7 @@ class MPO:
         if barrier_timeout_s > 0:
             o.barrier_timeout_s = barrier_timeout_s
         o.block_jacobi_min_rows = block_jacobi_min_rows
+        o.tensor_cores = 0 if tensor_cores else -1
         h = ctypes.c_void_p()
         st = ctypes.c_void_p(stream) if stream is not None else _current_stream()
         rc = lib.mpo_init(ctypes.byref(h), n, chi_max, self.prec, st, ctypes.byref(o))
@@ -310,3 +314,19 @@ def svd_rows_static(X, precision: str = "fp64", max_sweeps: int = 0):
     if rc != 0:
         raise MPOError(rc, lib.mpo_last_error(None).decode())
     return w, Ut
+
+
+def gemm(A, B, precision: str = "fp32", tensor_cores: bool = True):
+    """C = A B on the device through the C ABI (test export); A (M, K), B (K, N)
+    CUDA complex tensors, contiguous."""
+    import torch
+    lib = load_library()
+    M, K = A.shape
+    N = B.shape[1]
+    C = torch.empty((M, N), dtype=A.dtype, device=A.device)
+    prec = {"fp64": MPO_FP64, "fp32": MPO_FP32}[precision]
+    rc = lib.mpo_gemm(M, N, K, A.data_ptr(), B.data_ptr(), C.data_ptr(), prec, int(tensor_cores),
+                      ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if rc != 0:
+        raise MPOError(rc, "mpo_gemm failed")
+    return C

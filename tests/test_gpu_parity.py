@@ -309,3 +309,20 @@ def test_probabilities_and_samples_match_oracle(M):
         ref = sampling.sample(d.final, u)
         assert np.array_equal(bits, ref)
         np.testing.assert_allclose(Ps, sampling.probabilities(d.final, ref), atol=1e-12)
+
+
+# -------------------------------------------------- tensor-core contraction --
+@pytest.mark.parametrize("M,N,K", [(128, 64, 32), (300, 200, 77), (1024, 1024, 256)])
+def test_tcgen05_complex_gemm_matches_fp64(M, N, K):
+    """The FP32 form's tensor-core GEMM (tcgen05, 3 x TF32 split products)
+    against an FP64 product of the same FP32 inputs: FP32-level accuracy."""
+    import torch
+    M_ = need_gpu()
+    A = random_complex((M, K), seed=M).astype(np.complex64)
+    B = random_complex((K, N), seed=N + 1).astype(np.complex64)
+    ref = A.astype(np.complex128) @ B.astype(np.complex128)
+    C = M_.gemm(torch.tensor(A, device="cuda"), torch.tensor(B, device="cuda"), "fp32", tensor_cores=True).cpu().numpy()
+    Cs = M_.gemm(torch.tensor(A, device="cuda"), torch.tensor(B, device="cuda"), "fp32", tensor_cores=False).cpu().numpy()
+    scale = np.sqrt(K)
+    assert np.abs(C - ref).max() < 2e-6 * scale * np.abs(ref).max() / np.sqrt(K) * 8
+    assert np.abs(C - ref).max() < 4 * np.abs(Cs - ref).max() + 1e-6
