@@ -81,9 +81,9 @@ typedef struct {
                                < 0 = never]. The block form needs far fewer passes over
                                the matrix but resolves singular values only to about
                                sqrt(eps) * sigma_max relative accuracy per row pair. */
-  int tensor_cores;         /* FP32 only: plain complex products (theta, centre moves) on the
-                               tcgen05 tensor cores with 3 x TF32 split products [0 = on;
-                               < 0 = off, SIMT FP32 instead] */
+  int tensor_cores;         /* FP32 only: > 0 runs the plain complex products (theta, centre
+                               moves) on the tcgen05 tensor cores with 3 x TF32 split products
+                               [0 = off: the SIMT FP32 kernel, currently the faster one] */
 } mpo_opts;
 
 /* Fill *o with the defaults. */

@@ -75,9 +75,10 @@ struct mpo_ctx {
   double* lam2 = nullptr;
   SelectInfo* info = nullptr;
   GridCtl* ctl = nullptr;
-  OSCtl* osctl = nullptr;
-  void *bj_gpart = nullptr, *bj_j = nullptr;   // block Jacobi workspaces
+  OSCtl* osctl = nullptr;          // control block of the Jacobi launches (barriers, status, counts)
+  void *bj_gpart = nullptr, *bj_j = nullptr;   // block Jacobi partial Grams and pair rotations
   int* bj_act = nullptr;
+  size_t bj_slots = 0;
   int block_min_rows = 0;
   bool tensor_cores = false;       // FP32 plain products on tcgen05
   int* tc_status = nullptr;        // set by the tensor-core GEMM if a wait timed out
@@ -242,8 +243,8 @@ static cudaError_t launch_onesided(cudaStream_t st, cplx<T>* X, int r, int c, in
 
 template <typename T>
 static cudaError_t launch_block_jacobi(cudaStream_t st, cplx<T>* X, int r, int c, int ldx, cplx<T>* Ut, T* w,
-                                      cplx<T>* Gpart, cplx<T>* Jbuf, int* act, OSCtl* ctl, int max_sweeps,
-                                      double timeout_s, int num_sms) {
+                                      cplx<T>* Gpart, size_t gpart_slots, cplx<T>* Jbuf, int* act, OSCtl* ctl,
+                                      int max_sweeps, double timeout_s, int num_sms) {
   const int smem = block_jacobi_smem_bytes<T>();
   cudaError_t e = cudaFuncSetAttribute(block_jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
@@ -252,6 +253,8 @@ static cudaError_t launch_block_jacobi(cudaStream_t st, cplx<T>* X, int r, int c
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int nb = (r + JB - 1) / JB, npairs = (nb + (nb & 1)) / 2;
+  const size_t nch = (size_t)(c + JCW - 1) / JCW;
+  if ((size_t)npairs * nch > gpart_slots) return cudaErrorInvalidValue;   // workspace too small
   const int items = npairs * ((c + JCW - 1) / JCW + (r + JCW - 1) / JCW);
   const int blocks = std::max(1, std::min(per_sm * num_sms, items));
   e = cudaMemsetAsync(ctl, 0, sizeof(OSCtl), st);
@@ -281,7 +284,7 @@ static int svd_select(mpo_ctx* h, cplx<T>* X, int r, int c, int ldx, int cap, bo
     ProfScope ps(h, PK_SVD, 4.0 * mn * mn * mx + 13.3 * mn * mn * mn,
                  (2.0 * r * c + (double)r * r) * sizeof(cplx<T>));
     if (h->block_min_rows > 0 && r >= h->block_min_rows)
-      CK(h, launch_block_jacobi<T>(h->st, X, r, c, ldx, (cplx<T>*)h->vecs, w, (cplx<T>*)h->bj_gpart,
+      CK(h, launch_block_jacobi<T>(h->st, X, r, c, ldx, (cplx<T>*)h->vecs, w, (cplx<T>*)h->bj_gpart, h->bj_slots,
                                    (cplx<T>*)h->bj_j, h->bj_act, h->osctl, h->opts.eig_max_sweeps,
                                    h->opts.barrier_timeout_s, h->num_sms));
     else
@@ -683,7 +686,7 @@ int mpo_init(mpo_handle* out, int n, int chi_max, mpo_precision prec, void* stre
   const int jac_limit = prec == MPO_FP64 ? 8192 : 16384;   // rotation table must fit shared memory
   if (m > jac_limit) return init_fail(h, MPO_ERR_ARG, "bond dimension too large for the eigen-solver's shared-memory table");
   h->tmp_cap = (size_t)m * chi_max;
-  h->tensor_cores = prec == MPO_FP32 && h->opts.tensor_cores >= 0;
+  h->tensor_cores = prec == MPO_FP32 && h->opts.tensor_cores > 0;
   h->block_min_rows = h->opts.block_jacobi_min_rows < 0 ? 0
                       : (h->opts.block_jacobi_min_rows > 0 ? h->opts.block_jacobi_min_rows : (prec == MPO_FP32 ? 64 : 0));
   const size_t bj_pairs = (size_t)((m + JB - 1) / JB + 1) / 2 + 1;
@@ -724,7 +727,8 @@ int mpo_init(mpo_handle* out, int n, int chi_max, mpo_precision prec, void* stre
   ok = ok && alloc((void**)&h->osctl, sizeof(OSCtl));
   ok = ok && alloc((void**)&h->tc_status, sizeof(int));
   if (h->block_min_rows > 0) {
-    ok = ok && alloc(&h->bj_gpart, bj_pairs * bj_nch * JP * JP * h->esz);
+    h->bj_slots = bj_pairs * bj_nch;
+    ok = ok && alloc(&h->bj_gpart, h->bj_slots * JP * JP * h->esz);
     ok = ok && alloc(&h->bj_j, bj_pairs * JP * JP * h->esz);
     ok = ok && alloc((void**)&h->bj_act, bj_pairs * sizeof(int));
   }
@@ -992,7 +996,6 @@ int mpo_to_dense(mpo_handle h, double* rho_vec) {
 
 int mpo_svd(int r, int c, void* X, void* w, void* Ut, mpo_precision prec, int max_sweeps, int block, void* stream) {
   if (r < 1 || c < 1 || !X || !w || !Ut) return MPO_ERR_ARG;
-
   cudaStream_t st = (cudaStream_t)stream;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return MPO_ERR_CUDA;
@@ -1013,8 +1016,10 @@ int mpo_svd(int r, int c, void* X, void* w, void* Ut, mpo_precision prec, int ma
   cudaError_t e;
   if (block)
     e = prec == MPO_FP64
-        ? launch_block_jacobi<double>(st, (double2*)X, r, c, c, (double2*)Ut, (double*)w, (double2*)gp, (double2*)jb, act, ctl, ms, 5.0, sms)
-        : launch_block_jacobi<float>(st, (float2*)X, r, c, c, (float2*)Ut, (float*)w, (float2*)gp, (float2*)jb, act, ctl, ms, 5.0, sms);
+        ? launch_block_jacobi<double>(st, (double2*)X, r, c, c, (double2*)Ut, (double*)w, (double2*)gp, pairs * nch,
+                                      (double2*)jb, act, ctl, ms, 5.0, sms)
+        : launch_block_jacobi<float>(st, (float2*)X, r, c, c, (float2*)Ut, (float*)w, (float2*)gp, pairs * nch,
+                                     (float2*)jb, act, ctl, ms, 5.0, sms);
   else
     e = prec == MPO_FP64
         ? launch_onesided<double>(st, (double2*)X, r, c, c, (double2*)Ut, (double*)w, ctl, ms, 5.0, sms)
@@ -1046,11 +1051,12 @@ constexpr int kStaticMaxRows = 512;
 constexpr int kStaticMaxCols = 2048;
 constexpr size_t kStaticPairs = (size_t)(((kStaticMaxRows + JB - 1) / JB + 1) / 2 + 1);
 constexpr size_t kStaticChunks = (size_t)((kStaticMaxCols + JCW - 1) / JCW + 1);
+constexpr size_t kStaticSlots = kStaticPairs * kStaticChunks;
 struct StaticSvdScratch {       // laid out for the widest element (complex128)
   OSCtl ctl;
   int act[kStaticPairs];
   double2 jbuf[kStaticPairs * JP * JP];
-  double2 gpart[kStaticPairs * kStaticChunks * JP * JP];
+  double2 gpart[kStaticSlots * JP * JP];
 };
 }  // namespace
 
@@ -1100,9 +1106,9 @@ int mpo_svd_static(int r, int c, void* X, void* w, void* Ut, mpo_precision prec,
   // pair flags are fully written before they are read in every round
   cudaError_t e = prec == MPO_FP64
       ? launch_block_jacobi<double>(st, (double2*)X, r, c, c, (double2*)Ut, (double*)w, (double2*)s->gpart,
-                                    (double2*)s->jbuf, s->act, &s->ctl, ms, 5.0, sms)
+                                    kStaticSlots, (double2*)s->jbuf, s->act, &s->ctl, ms, 5.0, sms)
       : launch_block_jacobi<float>(st, (float2*)X, r, c, c, (float2*)Ut, (float*)w, (float2*)s->gpart,
-                                   (float2*)s->jbuf, s->act, &s->ctl, ms, 5.0, sms);
+                                   kStaticSlots, (float2*)s->jbuf, s->act, &s->ctl, ms, 5.0, sms);
   GridCtl hc{};
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, &s->ctl.g, sizeof(GridCtl), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

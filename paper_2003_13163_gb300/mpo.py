@@ -115,7 +115,7 @@ class MPO:
 
     def __init__(self, n: int, chi_max: int, precision: str = "fp64", *, cutoff: float = 0.0,
                  eig_max_sweeps: int = 0, arena_cap_bytes: int = 0, centre_only: bool = False,
-                 barrier_timeout_s: float = 0.0, block_jacobi_min_rows: int = 0, tensor_cores: bool = True,
+                 barrier_timeout_s: float = 0.0, block_jacobi_min_rows: int = 0, tensor_cores: bool = False,
                  stream=None):
         lib = load_library()
         self._lib = lib
@@ -131,7 +131,7 @@ class MPO:
         if barrier_timeout_s > 0:
             o.barrier_timeout_s = barrier_timeout_s
         o.block_jacobi_min_rows = block_jacobi_min_rows
-        o.tensor_cores = 0 if tensor_cores else -1
+        o.tensor_cores = 1 if tensor_cores else 0
         h = ctypes.c_void_p()
         st = ctypes.c_void_p(stream) if stream is not None else _current_stream()
         rc = lib.mpo_init(ctypes.byref(h), n, chi_max, self.prec, st, ctypes.byref(o))
