@@ -307,7 +307,8 @@ def main():
             "gpu_launches": int(sum(v["launches"] for v in classes.values())),
             "roofline": roofline,
             "kernels": kernels,
-            "svd_sweeps_per_launch": prof["_sweeps"] / max(1, prof.get("svd_jacobi", {}).get("launches", 1)),
+            "svd_sweeps_per_launch": prof["_sweeps"] / max(1, sum(prof.get(k, {}).get("launches", 0)
+                                                                    for k in ("svd_gate", "svd_sweep"))),
             "block_jacobi_phase_ms": {k: round(v, 1) for k, v in prof["_block_jacobi_phase_ms"].items()},
             "e2e": {"value": e2e_value, "unit": "gates/s", "h2d_bytes_per_step": h2d // K,
                     "d2h_bytes_per_step": d2h // K}}

@@ -186,8 +186,10 @@ size_t mpo_device_bytes(mpo_handle h);
  * counterpart (it is a measurement aid). */
 int mpo_profile(mpo_handle h, int enable);
 
-/* Totals for kernel class cls (0 .. 6: svd_jacobi, cgemm, superop, select,
- * gather, transpose, trace) since the last mpo_profile(h, 1): summed event
+/* Totals for kernel class cls (0 .. 8: svd_gate (the truncated SVD of a
+ * gate), svd_sweep (the SVDs of centre moves and Schmidt sweeps), cgemm,
+ * superop, select, gather, transpose, trace, tc_cgemm) since the last
+ * mpo_profile(h, 1): summed event
  * durations in ms, launch count, and the algorithmic flops and bytes of those
  * launches as the library counts them (an SVD of an r x c matrix counts the
  * Gram-plus-dense-eigensolver work 4 min^2 max + 13.3 min^3, a complex GEMM
@@ -229,6 +231,12 @@ int mpo_eigh(int m, void *A, void *w, void *V, mpo_precision prec, int max_sweep
  * (<= 64) is reached. */
 int mpo_svd(int r, int c, void *X, void *w, void *Ut, mpo_precision prec, int max_sweeps, int block,
             void *cuda_stream);
+
+/* Statistics of the last mpo_svd call made on the calling thread: the sweeps
+ * it ran and, for the block variant, the wall time (ms) of its three phases
+ * (Gram partials, pair solves, rotation apply; grid-barrier waits included,
+ * zeros for the row-pair variant). Either pointer may be NULL (host). */
+int mpo_svd_last_stats(int *sweeps, double *phase_ms3);
 
 /* Block one-sided Jacobi SVD that allocates nothing (the paper has no
  * counterpart; this is a deployment aid).

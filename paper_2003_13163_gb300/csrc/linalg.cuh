@@ -635,6 +635,16 @@ constexpr int JB = 16;           // rows per block
 constexpr int JP = 2 * JB;       // rows per pair
 constexpr int JCW = 512;         // columns per Gram / apply work item
 
+// Integer state of the block Jacobi for r rows: the per-pair rotate flags of
+// a round, then for each block the round stamp of its last rotation, then
+// for each block pair (P, Q) the stamp of the round that last found it
+// orthogonal (N x N, N = the padded block count).
+__host__ __device__ constexpr size_t bj_state_ints(int r) {
+  return (size_t)(((r + JB - 1) / JB + (((r + JB - 1) / JB) & 1)) / 2) +
+         (size_t)((r + JB - 1) / JB + (((r + JB - 1) / JB) & 1)) +
+         (size_t)((r + JB - 1) / JB + (((r + JB - 1) / JB) & 1)) * (size_t)((r + JB - 1) / JB + (((r + JB - 1) / JB) & 1));
+}
+
 
 // In-CTA cyclic Jacobi of the pair's 2JB x 2JB Gram in the working precision
 // TI (FP64 arithmetic runs at 1/64 of the FP32 rate on this part, so nothing
@@ -646,79 +656,126 @@ template <typename TI> __device__ __forceinline__ TI rsqrt_fast(TI x);
 template <> __device__ __forceinline__ float rsqrt_fast<float>(float x) { return rsqrtf(x); }
 template <> __device__ __forceinline__ double rsqrt_fast<double>(double x) { return rsqrt(x); }
 
+// Rotation parameters of the 2 x 2 Hermitian block [[a, g], [conj g, b]]
+// (rows p, q of G): c, s real and u = g / |g|, chosen so that the rotation
+// R = [[c, s], [-s conj(u), c conj(u)]] zeroes the off-diagonal entry of
+// R^H G R; s = 0 when |g|^2 <= max(tol^2 |a b|, floor^2) (square-root free
+// skip test).
 template <typename TI>
-__device__ void bj_inner_eig(cplx<TI>* Gs /*JP x JP, ld JP+1*/, cplx<TI>* Vs /*JP x JP, ld JP+1*/, double tol,
-                             double floor_abs, int max_sweeps) {
+__device__ __forceinline__ void bj_rot_params(const cplx<TI>* G, int p, int q, TI tol2, TI flo2, TI& c_, TI& s_,
+                                              TI& ur, TI& ui) {
   constexpr int LD = JP + 1;
-  __shared__ TI rc[JP / 2], rs[JP / 2], rur[JP / 2], rui[JP / 2];
-  __shared__ int rp[JP / 2], rq[JP / 2];
-  const int tid = threadIdx.x;
+  const TI a_ = G[p * LD + p].x, b_ = G[q * LD + q].x;
+  const TI gx = G[p * LD + q].x, gy = G[p * LD + q].y;
+  const TI g2 = gx * gx + gy * gy;
+  c_ = TI(1); s_ = TI(0); ur = TI(1); ui = TI(0);
+  if (g2 > fmax(tol2 * fabs(a_ * b_), flo2) && g2 > TI(0)) {
+    const TI inv = rsqrt_fast<TI>(g2);                              // 1 / |g|
+    const TI zeta = (b_ - a_) * TI(0.5) * inv;
+    TI t;
+    if constexpr (sizeof(TI) == 4) {
+      // FP32: approximate divide and square root (a few ulp); any t gives
+      // an exactly normalised (c, s) up to rsqrt rounding, and an inexact
+      // angle only leaves a slightly larger off-diagonal for later rounds
+      const float az = fabsf(zeta);
+      if (az > 1.0f / eps_of<float>::value) t = __fdividef(0.5f, zeta);
+      else {
+        const float q = fmaf(zeta, zeta, 1.0f);
+        t = __fdividef(1.0f, az + q * rsqrtf(q));
+        if (!(zeta >= 0.0f)) t = -t;
+      }
+    } else {
+      if (fabs(zeta) > TI(1) / eps_of<TI>::value) t = TI(0.5) / zeta;
+      else t = (zeta >= TI(0) ? TI(1) : TI(-1)) / (fabs(zeta) + sqrt(TI(1) + zeta * zeta));
+    }
+    c_ = rsqrt_fast<TI>(TI(1) + t * t);
+    s_ = t * c_;
+    ur = gx * inv; ui = gy * inv;
+  }
+}
+
+// One round of the cyclic parallel Jacobi as 2 x 2 block updates: the round's
+// JP/2 disjoint rotations partition the indices into pairs, so the JP x JP
+// matrix splits into (JP/2)^2 blocks B_ab = G[{p_a, q_a}][{p_b, q_b}], each
+// updated on its own as B_ab <- R_a^H B_ab R_b. Thread (a, b) derives both
+// rotations from the old matrix and writes the new block into the other
+// buffer, so a round needs one barrier instead of three (parameters, column
+// pass, row pass). Requires blockDim.x == (JP/2)^2.
+//
+// In-CTA cyclic Jacobi of the pair's 2JB x 2JB Gram in the working precision
+// TI (FP64 arithmetic runs at 1/64 of the FP32 rate on this part, so nothing
+// here is promoted). The tolerance is set at the rounding level of TI and the
+// sweep count is capped, because J is re-derived in every outer round and an
+// inexact inner solve only costs outer sweeps. The rounding drift of the
+// accumulated rotations is removed afterwards by bj_polish_unitary. G0 holds
+// the input; G1 is scratch of the same shape; both are overwritten.
+template <typename TI>
+__device__ void bj_inner_eig(cplx<TI>* G0, cplx<TI>* G1, cplx<TI>* Vs /*JP x JP, ld JP+1*/, double tol,
+                             double floor_abs, int max_sweeps) {
+  constexpr int LD = JP + 1, NR = JP / 2;
+  static_assert(NR * NR == 256, "one thread per 2 x 2 block");
+  const int tid = threadIdx.x, ia = tid / NR, ib = tid % NR;
   for (int e = tid; e < JP * JP; e += blockDim.x) {
     const int i = e / JP, j = e % JP;
     Vs[i * LD + j] = mk<TI>(i == j ? TI(1) : TI(0), TI(0));
   }
   __syncthreads();
   const TI tol2 = (TI)(tol * tol), flo2 = (TI)(floor_abs * floor_abs);
+  cplx<TI>* Gc = G0;
+  cplx<TI>* Gn = G1;
   for (int sw = 0; sw < max_sweeps; ++sw) {
     int any = 0;
     for (int rd = 0; rd < JP - 1; ++rd) {
-      // rotation table of the round (the pairs and their parameters); the
-      // square-root-free test |g|^2 > max(tol^2 a b, floor^2) decides a skip
-      int act = 0;
-      if (tid < JP / 2) {
-        int p = rr_player(tid, rd, JP), q = rr_player(JP - 1 - tid, rd, JP);
-        if (p > q) { int t_ = p; p = q; q = t_; }
-        rp[tid] = p; rq[tid] = q;
-        const TI a_ = Gs[p * LD + p].x, b_ = Gs[q * LD + q].x;
-        const TI gx = Gs[p * LD + q].x, gy = Gs[p * LD + q].y;
-        const TI g2 = gx * gx + gy * gy;
-        TI c_ = TI(1), s_ = TI(0), ur = TI(1), ui = TI(0);
-        if (g2 > fmax(tol2 * fabs(a_ * b_), flo2) && g2 > TI(0)) {
-          const TI inv = rsqrt_fast<TI>(g2), ag = g2 * inv;          // 1/|g|, |g|
-          const TI zeta = (b_ - a_) * TI(0.5) * inv;
-          TI t;
-          if (fabs(zeta) > TI(1) / eps_of<TI>::value) t = TI(0.5) / zeta;
-          else t = (zeta >= TI(0) ? TI(1) : TI(-1)) / (fabs(zeta) + sqrt(TI(1) + zeta * zeta));
-          c_ = rsqrt_fast<TI>(TI(1) + t * t);
-          s_ = t * c_;
-          ur = gx * inv; ui = gy * inv;
-          (void)ag;
-          act = (s_ != TI(0));
+      int pa = rr_player(ia, rd, JP), qa = rr_player(JP - 1 - ia, rd, JP);
+      if (pa > qa) { const int t_ = pa; pa = qa; qa = t_; }
+      int pb = rr_player(ib, rd, JP), qb = rr_player(JP - 1 - ib, rd, JP);
+      if (pb > qb) { const int t_ = pb; pb = qb; qb = t_; }
+      // lane l of every warp derives rotation l % NR; threads fetch the two
+      // they need by shuffle (no block barrier for a shared table)
+      TI cl, sl, url, uil;
+      {
+        const int lr = (tid & 31) % NR;
+        int pl = rr_player(lr, rd, JP), ql = rr_player(JP - 1 - lr, rd, JP);
+        if (pl > ql) { const int t_ = pl; pl = ql; ql = t_; }
+        bj_rot_params<TI>(Gc, pl, ql, tol2, flo2, cl, sl, url, uil);
+      }
+      const TI ca = __shfl_sync(0xffffffffu, cl, ia), sa = __shfl_sync(0xffffffffu, sl, ia);
+      const TI ura = __shfl_sync(0xffffffffu, url, ia), uia = __shfl_sync(0xffffffffu, uil, ia);
+      const TI cb = __shfl_sync(0xffffffffu, cl, ib), sb = __shfl_sync(0xffffffffu, sl, ib);
+      const TI urb = __shfl_sync(0xffffffffu, url, ib), uib = __shfl_sync(0xffffffffu, uil, ib);
+      cplx<TI> b00 = Gc[pa * LD + pb], b01 = Gc[pa * LD + qb], b10 = Gc[qa * LD + pb], b11 = Gc[qa * LD + qb];
+      if (sb != TI(0)) {        // columns: [x y] <- [c x - s conj(u) y, s x + c conj(u) y]
+        const cplx<TI> ub = mk<TI>(urb, -uib);
+        const cplx<TI> y0 = cmul<TI>(ub, b01), y1 = cmul<TI>(ub, b11);
+        b01 = mk<TI>(sb * b00.x + cb * y0.x, sb * b00.y + cb * y0.y);
+        b00 = mk<TI>(cb * b00.x - sb * y0.x, cb * b00.y - sb * y0.y);
+        b11 = mk<TI>(sb * b10.x + cb * y1.x, sb * b10.y + cb * y1.y);
+        b10 = mk<TI>(cb * b10.x - sb * y1.x, cb * b10.y - sb * y1.y);
+      }
+      if (sa != TI(0)) {        // rows: [x; y] <- [c x - s u y; s x + c u y]
+        const cplx<TI> ua = mk<TI>(ura, uia);
+        const cplx<TI> y0 = cmul<TI>(ua, b10), y1 = cmul<TI>(ua, b11);
+        b10 = mk<TI>(sa * b00.x + ca * y0.x, sa * b00.y + ca * y0.y);
+        b00 = mk<TI>(ca * b00.x - sa * y0.x, ca * b00.y - sa * y0.y);
+        b11 = mk<TI>(sa * b01.x + ca * y1.x, sa * b01.y + ca * y1.y);
+        b01 = mk<TI>(ca * b01.x - sa * y1.x, ca * b01.y - sa * y1.y);
+        if (ia == ib) {         // the rotated diagonal block: exact zeros, real diagonal
+          b01 = czero<TI>(); b10 = czero<TI>(); b00.y = TI(0); b11.y = TI(0);
         }
-        rc[tid] = c_; rs[tid] = act ? s_ : TI(0); rur[tid] = ur; rui[tid] = ui;
       }
-      if (!__syncthreads_or(act)) continue;   // nothing to rotate this round
-      any = 1;
-      for (int e = tid; e < 2 * JP * (JP / 2); e += blockDim.x) {
-        const int pi = e % (JP / 2), row = e / (JP / 2);
-        const TI s_ = rs[pi];
-        if (s_ == TI(0)) continue;
-        const int p = rp[pi], q = rq[pi];
-        cplx<TI>* R = row < JP ? Gs + row * LD : Vs + (row - JP) * LD;
-        const TI c_ = rc[pi];
-        const cplx<TI> x = R[p], y = R[q];
-        const cplx<TI> uy = cmul<TI>(mk<TI>(rur[pi], -rui[pi]), y);
-        R[p] = mk<TI>(c_ * x.x - s_ * uy.x, c_ * x.y - s_ * uy.y);
-        R[q] = mk<TI>(s_ * x.x + c_ * uy.x, s_ * x.y + c_ * uy.y);
+      Gn[pa * LD + pb] = b00; Gn[pa * LD + qb] = b01; Gn[qa * LD + pb] = b10; Gn[qa * LD + qb] = b11;
+      if (sb != TI(0)) {        // V <- V R_b on rows ia and ia + NR
+        const cplx<TI> ub = mk<TI>(urb, -uib);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          cplx<TI>* R = Vs + (ia + h * NR) * LD;
+          const cplx<TI> x = R[pb], uy = cmul<TI>(ub, R[qb]);
+          R[pb] = mk<TI>(cb * x.x - sb * uy.x, cb * x.y - sb * uy.y);
+          R[qb] = mk<TI>(sb * x.x + cb * uy.x, sb * x.y + cb * uy.y);
+        }
       }
-      __syncthreads();
-      for (int e = tid; e < JP * (JP / 2); e += blockDim.x) {
-        const int pi = e % (JP / 2), j = e / (JP / 2);
-        const TI s_ = rs[pi];
-        if (s_ == TI(0)) continue;
-        const int p = rp[pi], q = rq[pi];
-        const TI c_ = rc[pi];
-        const cplx<TI> x = Gs[p * LD + j], y = Gs[q * LD + j];
-        const cplx<TI> uy = cmul<TI>(mk<TI>(rur[pi], rui[pi]), y);
-        cplx<TI> np_ = mk<TI>(c_ * x.x - s_ * uy.x, c_ * x.y - s_ * uy.y);
-        cplx<TI> nq_ = mk<TI>(s_ * x.x + c_ * uy.x, s_ * x.y + c_ * uy.y);
-        if (j == q) np_ = czero<TI>();
-        if (j == p) { nq_ = czero<TI>(); np_.y = TI(0); }
-        if (j == q) nq_.y = TI(0);
-        Gs[p * LD + j] = np_;
-        Gs[q * LD + j] = nq_;
-      }
-      __syncthreads();
+      any |= __syncthreads_or(sb != TI(0));
+      cplx<TI>* t_ = Gc; Gc = Gn; Gn = t_;
     }
     if (!any) break;
   }
@@ -757,20 +814,74 @@ __device__ void bj_polish_unitary(cplx<TI>* Vs, cplx<TI>* S, cplx<TI>* W) {
   __syncthreads();
 }
 
+// Newton-Schulz steps until V is unitary to rounding: each step first forms
+// S = V^H V and tests max |S - I| <= tol, then applies the step; the loop
+// ends after the first step taken from a state that passed the test (leaving
+// a defect of about tol^2 plus rounding) or after max_steps steps. The
+// iteration converges for |S - I| < 1 (Higham, Functions of Matrices, 8.3).
+template <typename TI>
+__device__ void bj_polish_unitary_to(cplx<TI>* Vs, cplx<TI>* S, cplx<TI>* W, TI tol, int max_steps) {
+  constexpr int LD = JP + 1;
+  const int tid = threadIdx.x;
+  for (int it = 0; it < max_steps; ++it) {
+    int bad = 0;
+    for (int e = tid; e < JP * JP; e += blockDim.x) {
+      const int i = e / JP, j = e % JP;
+      cplx<TI> acc = czero<TI>();
+#pragma unroll 8
+      for (int k = 0; k < JP; ++k) cfma<TI>(acc, cconj<TI>(Vs[k * LD + i]), Vs[k * LD + j]);
+      S[i * LD + j] = acc;
+      if (!(fabs(acc.x - (i == j ? TI(1) : TI(0))) <= tol && fabs(acc.y) <= tol)) bad = 1;
+    }
+    const int any_bad = __syncthreads_or(bad);
+    for (int e = tid; e < JP * JP; e += blockDim.x) {
+      const int i = e / JP, j = e % JP;
+      cplx<TI> acc = czero<TI>();
+#pragma unroll 8
+      for (int k = 0; k < JP; ++k) {
+        cplx<TI> m = cscale<TI>(S[k * LD + j], TI(-0.5));
+        if (k == j) m.x += TI(1.5);
+        cfma<TI>(acc, Vs[i * LD + k], m);
+      }
+      W[i * LD + j] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < JP * JP; e += blockDim.x) Vs[(e / JP) * LD + (e % JP)] = W[(e / JP) * LD + (e % JP)];
+    __syncthreads();
+    if (!any_bad) break;
+  }
+}
+
+// Asynchronous global -> shared copies (cp.async): BYTES per copy, the tail
+// beyond src_bytes zero-filled, so rows past the matrix read as zeros.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_zfill(void* dst, const void* src, int src_bytes) {
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" :: "r"(smem_addr(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" :: "r"(smem_addr(dst)), "l"(src), "n"(BYTES),
+                 "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" :: "n"(N) : "memory"); }
+
 template <typename T> struct BJ_GW { static constexpr int value = sizeof(T) == 4 ? 128 : 64; };
+constexpr int BJ_NB = 4;   // phase-G staging ring: sub-chunks in flight per CTA
 __device__ __forceinline__ bool tid_is_zero() { return threadIdx.x == 0; }
 
-// Dynamic shared memory of block_jacobi_kernel<T>: the larger of two staging
-// tiles, the phase E/A matrices and the cross-block reduction buffer.
+// Dynamic shared memory of block_jacobi_kernel<T>: the larger of the phase-G
+// staging ring and the phase E/A matrices, then the cross-block reduction
+// buffer.
 template <typename T>
 constexpr int block_jacobi_smem_bytes() {
   constexpr int GW = BJ_GW<T>::value;
-  constexpr int TS = GW + 16 / (int)sizeof(cplx<T>);
-  constexpr int TILES = 2 * JP * TS * (int)sizeof(cplx<T>);
+  constexpr int TS = GW + 1;
+  constexpr int RING = BJ_NB * JP * TS * (int)sizeof(cplx<T>);
   constexpr int GV = 3 * JP * (JP + 1) * (int)sizeof(cplx<T>);
   constexpr int RED = 8 * 16 * 40 * (int)sizeof(T);
-  constexpr int M1 = TILES > GV ? TILES : GV;
-  return M1 > RED ? M1 : RED;
+  return (RING > GV ? RING : GV) + RED;
 }
 
 template <typename T>
@@ -778,18 +889,23 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
                                                             cplx<T>* Gpart, cplx<T>* Jbuf, int* act_flag, OSCtl* ctl,
                                                             int max_sweeps, T tol_rel, T floor_rel, long long timeout_ns) {
   constexpr int LD = JP + 1;
-  // Dynamic shared memory (block_jacobi_smem_bytes<T>()): two phase-G tiles
-  // of JP rows x TS columns (double buffer); phases E and A reuse the same
-  // bytes for the pair Gram Gs, the rotation Vs and the polish scratch.
+  // Dynamic shared memory (block_jacobi_smem_bytes<T>()): a ring of BJ_NB
+  // phase-G tiles of JP rows x TS columns; phases E and A reuse the same
+  // bytes for the pair Gram Gs, the rotation Vs and the polish scratch; the
+  // cross-block reduction buffer follows.
   constexpr int GW = BJ_GW<T>::value;                    // staged columns in phase G
-  constexpr int TS = GW + 16 / (int)sizeof(cplx<T>);     // padded row stride (elements)
+  // padded row stride: GW + 1 puts the rows that one warp reads at the same
+  // column in distinct banks (8-byte rows at 2 x 129 words, 16-byte at 4 x 65)
+  constexpr int TS = GW + 1;
+  constexpr int RING = BJ_NB * JP * TS * (int)sizeof(cplx<T>), GV = 3 * JP * (JP + 1) * (int)sizeof(cplx<T>);
   extern __shared__ __align__(128) unsigned char smraw[];
-  cplx<T>* tiles[2] = {reinterpret_cast<cplx<T>*>(smraw), reinterpret_cast<cplx<T>*>(smraw) + JP * TS};
+  cplx<T>* ring = reinterpret_cast<cplx<T>*>(smraw);
+  T* red = reinterpret_cast<T*>(smraw + (RING > GV ? RING : GV));   // [8][16][40]
   cplx<T>* Gs = reinterpret_cast<cplx<T>*>(smraw);     // phase E: the pair Gram; phase A: J^H or J^T
   cplx<T>* Vs = Gs + JP * LD;
 
   __shared__ T s_gmax;
-  cplx<T>* Js = Gs;
+  cplx<T>* Js = reinterpret_cast<cplx<T>*>(red);        // phase A: J^H or J^T (ld JP+1)
   __shared__ T s_floor;
   const int nb = (r + JB - 1) / JB, N = nb + (nb & 1), npairs = N / 2;
   const int nch = (c + JCW - 1) / JCW, nchu = (r + JCW - 1) / JCW;
@@ -803,6 +919,12 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
     const size_t i = e / r, j = e % r;
     stcg(&Ut[e], mk<T>(i == j ? T(1) : T(0), T(0)));
   }
+  // round stamps (round g = sweep (N - 1) + rd + 1): a pair whose blocks are
+  // both unchanged since the round that found it orthogonal stays orthogonal,
+  // so cross-only sweeps skip its Gram and its test
+  int* last_mod = act_flag + npairs;
+  int* last_clean = last_mod + N;
+  for (size_t e = gtid; e < (size_t)N + (size_t)N * N; e += gthreads) last_mod[e] = 0;
   for (long i = gwarp; i < r; i += nwarps) {
     T s = T(0);
     for (int j = lane; j < c; j += 32) { const cplx<T> x = ldcg(&X[(size_t)i * ldx + j]); s += x.x * x.x + x.y * x.y; }
@@ -832,11 +954,54 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
       // diagonal blocks are taken as diagonal. The chunk is staged GW columns
       // at a time with every load in flight before the first store.
       const bool full_gram = (sweep == 0) || verify;
-      for (long item = blockIdx.x; item < (long)npairs * nch; item += nblk) {
+      const long nitems = (long)npairs * nch;
+      // The CTA's work is the sequence of (item, sub-chunk) stages of its
+      // items; a ring of BJ_NB tiles keeps BJ_NB stages in flight (cp.async,
+      // no register staging), refilling each tile as soon as its stage has
+      // been consumed, across item boundaries.
+      const int gstamp = sweep * (N - 1) + rd + 1;
+      auto pair_dirty = [&](int P_, int Q_) -> bool {
+        return __ldcg(&last_clean[(size_t)P_ * N + Q_]) <= max(__ldcg(&last_mod[P_]), __ldcg(&last_mod[Q_]));
+      };
+      auto item_valid = [&](long it) -> bool {
+        const int pi_ = (int)(it / nch);
+        int P_ = rr_player(pi_, rd, N), Q_ = rr_player(N - 1 - pi_, rd, N);
+        if (P_ > Q_) { const int t_ = P_; P_ = Q_; Q_ = t_; }
+        return Q_ < nb && (full_gram || pair_dirty(P_, Q_));
+      };
+      long p_item = blockIdx.x;   // producer cursor
+      int p_sub = 0;
+      while (p_item < nitems && !item_valid(p_item)) p_item += nblk;
+      auto issue = [&](int buf) {
+        if (p_item >= nitems) return;
+        const int pi_ = (int)(p_item / nch), ch_ = (int)(p_item % nch);
+        int P_ = rr_player(pi_, rd, N), Q_ = rr_player(N - 1 - pi_, rd, N);
+        if (P_ > Q_) { const int t_ = P_; P_ = Q_; Q_ = t_; }
+        const int c0_ = ch_ * JCW, c1_ = min(c, c0_ + JCW), k0 = c0_ + p_sub * GW;
+        cplx<T>* tile = ring + buf * JP * TS;
+        constexpr int PER = JP * GW / 256;
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+          const int e_ = tid + 256 * u, i = e_ / GW, k = e_ % GW;
+          const int row = (i < JB ? P_ * JB + i : Q_ * JB + (i - JB));
+          const bool in = row < r && k0 + k < c1_;
+          cp_async_zfill<(int)sizeof(cplx<T>)>(&tile[i * TS + k], in ? (const void*)&X[(size_t)row * ldx + k0 + k]
+                                                                     : (const void*)X,
+                                               in ? (int)sizeof(cplx<T>) : 0);
+        }
+        if (++p_sub == (c1_ - c0_ + GW - 1) / GW) {
+          p_sub = 0;
+          do { p_item += nblk; } while (p_item < nitems && !item_valid(p_item));
+        }
+      };
+#pragma unroll
+      for (int q = 0; q < BJ_NB; ++q) { issue(q); cp_async_commit(); }
+      int jseq = 0;               // consumer position in the stage sequence
+      for (long item = blockIdx.x; item < nitems; item += nblk) {
+        if (!item_valid(item)) continue;
         const int pi = (int)(item / nch), ch = (int)(item % nch);
         int P = rr_player(pi, rd, N), Q = rr_player(N - 1 - pi, rd, N);
         if (P > Q) { int t_ = P; P = Q; Q = t_; }
-        if (Q >= nb) continue;
         // full: thread (ti, tj) owns G[ti + 16a][tj + 16b];
         // cross: k-slice g = tid / 16 (k = g, g + 16, ...), member m = tid % 16
         // owns C[4 mi + i][4 mj + j], mi = m / 4, mj = m % 4, and the norms of
@@ -854,30 +1019,10 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
         }
         const int c0 = ch * JCW, c1 = min(c, c0 + JCW);
         const int nsub = (c1 - c0 + GW - 1) / GW;
-        // register staging with one sub-chunk of prefetch: the loads of
-        // sub-chunk s+1 are in flight while sub-chunk s is computed
-        constexpr int PER = JP * GW / 256;
-        cplx<T> v[PER];
-        auto load = [&](int s) {
-          const int k0 = c0 + s * GW;
-#pragma unroll
-          for (int u = 0; u < PER; ++u) {
-            const int e = tid + 256 * u, i = e / GW, k = e % GW;
-            const int row = (i < JB ? P * JB + i : Q * JB + (i - JB));
-            v[u] = (row < r && k0 + k < c1) ? ldcg(&X[(size_t)row * ldx + k0 + k]) : czero<T>();
-          }
-        };
-        __syncthreads();
-        load(0);
-        for (int s = 0; s < nsub; ++s) {
-          cplx<T>* tile = tiles[s & 1];
-#pragma unroll
-          for (int u = 0; u < PER; ++u) {
-            const int e = tid + 256 * u, i = e / GW, k = e % GW;
-            tile[i * TS + k] = v[u];
-          }
+        for (int s = 0; s < nsub; ++s, ++jseq) {
+          cp_async_wait<BJ_NB - 1>();
           __syncthreads();
-          if (s + 1 < nsub) load(s + 1);
+          const cplx<T>* tile = ring + (jseq % BJ_NB) * JP * TS;
           const int kn = min(GW, c1 - (c0 + s * GW));
           if (full_gram) {
 #pragma unroll 4
@@ -904,8 +1049,10 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
               }
             }
           }
+          __syncthreads();                      // the tile is free: refill it
+          issue(jseq % BJ_NB);
+          cp_async_commit();
         }
-        __syncthreads();
         cplx<T>* Gp = Gpart + ((size_t)pi * nch + ch) * JP * JP;
         if (full_gram) {
 #pragma unroll
@@ -917,7 +1064,6 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
           // same input always gives the same factorisation): half-warp pairs
           // by shuffle, then the 8 warps through shared memory
           constexpr int NV = 40;                                 // 16 complex + 4 + 4 norms
-          T* red = reinterpret_cast<T*>(smraw);                  // [8][16][NV]
           T vals[NV];
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
@@ -954,13 +1100,15 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
           __syncthreads();
         }
       }
+      cp_async_wait<0>();
+      __syncthreads();
       if (!grid_barrier(&ctl->g, nblk, timeout_ns)) return;
       if (blockIdx.x == 0 && tid == 0) { unsigned long long t2 = global_timer_ns(); ctl->phase_ns[0] += t2 - tph; tph = t2; }
       // ---- phase E: per pair, reduce, test, inner eigen-solve ---------------
       for (long pi = blockIdx.x; pi < npairs; pi += nblk) {
         int P = rr_player((int)pi, rd, N), Q = rr_player(N - 1 - (int)pi, rd, N);
         if (P > Q) { int t_ = P; P = Q; Q = t_; }
-        if (Q >= nb) { if (tid == 0) act_flag[pi] = 0; continue; }
+        if (Q >= nb || (!full_gram && !pair_dirty(P, Q))) { if (tid == 0) act_flag[pi] = 0; continue; }
         for (int e = tid; e < JP * JP; e += blockDim.x) {
           double sr = 0.0, si = 0.0;
           const cplx<T>* src = Gpart + (size_t)pi * nch * JP * JP + e;
@@ -987,58 +1135,169 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
         __syncthreads();
         const int need = s_need;
         if (need) {
-          if (tid == 0) {
-            T gm = T(0);
-            for (int i = 0; i < JP; ++i) gm = fmax(gm, Gs[i * LD + i].x);
-            s_gmax = gm;
+          // Near convergence the pair Gram is diag + a small cross block: one
+          // first-order step J = I + E, E_ij = G_ij / (G_jj - G_ii) on the
+          // cross entries (E skew-Hermitian), made unitary to rounding by
+          // Newton-Schulz steps (J^H J = I - E^2 to start), leaves O(|E|^2)
+          // off-diagonals -- quadratic like the Jacobi endgame but with O(1)
+          // sequential steps. Taken when every cross |E_ij| < 0.01 (so
+          // |J^H J - I| <= 512 * 1e-4 and the polish converges in a few
+          // steps) outside full-Gram sweeps; else the inner solve.
+          int first_order = 0;
+          if (!full_e) {
+            int ok = 1;
+            for (int e = tid; e < JB * JB; e += blockDim.x) {
+              const int i = e / JB, j = JB + e % JB;
+              const double gap = fabs((double)Gs[j * LD + j].x - (double)Gs[i * LD + i].x);
+              const double g = hypot((double)Gs[i * LD + j].x, (double)Gs[i * LD + j].y);
+              if (!(g < 0.01 * gap)) ok = 0;
+            }
+            first_order = __syncthreads_and(ok);
           }
-          __syncthreads();
-          bj_inner_eig<T>(Gs, Vs, 4.0 * (double)eps_of<T>::value * sqrt((double)JP),
-                          32.0 * (double)eps_of<T>::value * (double)s_gmax, 3);
-          // FP32: remove the rounding drift of J (FP64 rotations keep it at 1e-16)
-          if constexpr (sizeof(T) == 4) bj_polish_unitary<T>(Vs, Gs, Vs + JP * LD);
+          if (first_order) {
+            for (int e = tid; e < JP * JP; e += blockDim.x) {
+              const int i = e / JP, j = e % JP;
+              cplx<T> v = mk<T>(i == j ? T(1) : T(0), T(0));
+              if (i < JB && j >= JB) {                 // E_ij = G_ij / (G_jj - G_ii)
+                const T den = Gs[j * LD + j].x - Gs[i * LD + i].x;
+                v = cscale<T>(Gs[i * LD + j], T(1) / den);
+              } else if (i >= JB && j < JB) {          // E_ij = -conj(E_ji)
+                const T den = Gs[i * LD + i].x - Gs[j * LD + j].x;
+                v = cscale<T>(cconj<T>(Gs[j * LD + i]), T(-1) / den);
+              }
+              Vs[i * LD + j] = v;
+            }
+            __syncthreads();
+            bj_polish_unitary_to<T>(Vs, Gs, Vs + JP * LD, T(8.0 * eps_of<T>::value * 5.66), 6);
+          } else {
+            if (tid == 0) {
+              T gm = T(0);
+              for (int i = 0; i < JP; ++i) gm = fmax(gm, Gs[i * LD + i].x);
+              s_gmax = gm;
+            }
+            __syncthreads();
+            bj_inner_eig<T>(Gs, Vs + JP * LD, Vs, 4.0 * (double)eps_of<T>::value * sqrt((double)JP),
+                            32.0 * (double)eps_of<T>::value * (double)s_gmax, 3);
+            // FP32: remove the rounding drift of J (FP64 rotations keep it at 1e-16)
+            if constexpr (sizeof(T) == 4) bj_polish_unitary<T>(Vs, Gs, Vs + JP * LD);
+          }
           for (int e = tid; e < JP * JP; e += blockDim.x) stcg(&Jbuf[(size_t)pi * JP * JP + e], Vs[(e / JP) * LD + (e % JP)]);
-          if (tid == 0) { act_flag[pi] = 1; atomicAdd(&ctl->active[sweep], 1); }
+          if (tid == 0) {
+            act_flag[pi] = 1;
+            last_mod[P] = gstamp;
+            last_mod[Q] = gstamp;
+            atomicAdd(&ctl->active[sweep], 1);
+          }
         } else if (tid == 0) {
           act_flag[pi] = 0;
+          last_clean[(size_t)P * N + Q] = gstamp;
         }
         __syncthreads();
       }
       if (!grid_barrier(&ctl->g, nblk, timeout_ns)) return;
       if (blockIdx.x == 0 && tid == 0) { unsigned long long t2 = global_timer_ns(); ctl->phase_ns[1] += t2 - tph; tph = t2; }
       // ---- phase A: X_PQ <- J^H X_PQ, Ut_PQ <- J^T Ut_PQ -----------------
-      for (long item = blockIdx.x; item < (long)npairs * (nch + nchu); item += nblk) {
-        const int pi = (int)(item / (nch + nchu)), ch = (int)(item % (nch + nchu));
-        if (!__ldcg(&act_flag[pi])) continue;
-        int P = rr_player(pi, rd, N), Q = rr_player(N - 1 - pi, rd, N);
-        if (P > Q) { int t_ = P; P = Q; Q = t_; }
-        const bool onU = ch >= nch;
-        cplx<T>* M = onU ? Ut : X;
-        const int ld = onU ? r : ldx, ncol = onU ? r : c;
-        const int c0 = (onU ? ch - nch : ch) * JCW, c1 = min(ncol, c0 + JCW);
-        for (int e = tid; e < JP * JP; e += blockDim.x) {
-          // Gs[i][k] = (J^H)[i][k] = conj(J[k][i])  or  (J^T)[i][k] = J[k][i]
-          const int i = e / JP, k = e % JP;
-          const cplx<T> v = ldcg(&Jbuf[(size_t)pi * JP * JP + k * JP + i]);
-          Js[i * LD + k] = onU ? v : cconj<T>(v);
-        }
-        __syncthreads();
-        for (int col = c0 + tid; col < c1; col += blockDim.x) {
-          cplx<T> xin[JP];
+      // Work items are (active pair, 512-column chunk of X or of Ut), staged
+      // GW columns at a time through the same cp.async ring as phase G. Each
+      // thread forms a 4 x (GW/32) complex micro-tile of the product: rows
+      // 4 ty .. 4 ty + 3 (J from shared memory, a broadcast within the warp)
+      // by columns tx + 32 b (consecutive across the warp), eight shared
+      // loads per 16 (FP32) complex multiply-adds.
+      {
+        constexpr int NBC = GW / 32;                         // columns per thread
+        const long aitems = (long)npairs * (nch + nchu);
+        auto a_valid = [&](long it) -> bool { return __ldcg(&act_flag[(int)(it / (nch + nchu))]) != 0; };
+        long p_item = blockIdx.x;
+        int p_sub = 0;
+        while (p_item < aitems && !a_valid(p_item)) p_item += nblk;
+        auto issue = [&](int buf) {
+          if (p_item >= aitems) return;
+          const int pi_ = (int)(p_item / (nch + nchu)), ch_ = (int)(p_item % (nch + nchu));
+          int P_ = rr_player(pi_, rd, N), Q_ = rr_player(N - 1 - pi_, rd, N);
+          if (P_ > Q_) { const int t_ = P_; P_ = Q_; Q_ = t_; }
+          const bool onU_ = ch_ >= nch;
+          const cplx<T>* M_ = onU_ ? Ut : X;
+          const int ld_ = onU_ ? r : ldx, ncol_ = onU_ ? r : c;
+          const int c0_ = (onU_ ? ch_ - nch : ch_) * JCW, c1_ = min(ncol_, c0_ + JCW), k0 = c0_ + p_sub * GW;
+          cplx<T>* tile = ring + buf * JP * TS;
+          constexpr int PER = JP * GW / 256;
 #pragma unroll
-          for (int k = 0; k < JP; ++k) {
-            const int row = (k < JB ? P * JB + k : Q * JB + (k - JB));
-            xin[k] = row < r ? ldcg(&M[(size_t)row * ld + col]) : czero<T>();
+          for (int u = 0; u < PER; ++u) {
+            const int e_ = tid + 256 * u, i = e_ / GW, k = e_ % GW;
+            const int row = (i < JB ? P_ * JB + i : Q_ * JB + (i - JB));
+            const bool in = row < r && k0 + k < c1_;
+            cp_async_zfill<(int)sizeof(cplx<T>)>(&tile[i * TS + k],
+                                                 in ? (const void*)&M_[(size_t)row * ld_ + k0 + k] : (const void*)M_,
+                                                 in ? (int)sizeof(cplx<T>) : 0);
           }
-#pragma unroll 2
-          for (int i = 0; i < JP; ++i) {
-            const int row = (i < JB ? P * JB + i : Q * JB + (i - JB));
-            cplx<T> acc = czero<T>();
+          if (++p_sub == (c1_ - c0_ + GW - 1) / GW) {
+            p_sub = 0;
+            do { p_item += nblk; } while (p_item < aitems && !a_valid(p_item));
+          }
+        };
 #pragma unroll
-            for (int k = 0; k < JP; ++k) cfma<T>(acc, Js[i * LD + k], xin[k]);
-            if (row < r) stcg(&M[(size_t)row * ld + col], acc);
+        for (int q = 0; q < BJ_NB; ++q) { issue(q); cp_async_commit(); }
+        const int ty = tid >> 5, tx = tid & 31;
+        int jseq = 0;
+        for (long item = blockIdx.x; item < aitems; item += nblk) {
+          if (!a_valid(item)) continue;
+          const int pi = (int)(item / (nch + nchu)), ch = (int)(item % (nch + nchu));
+          int P = rr_player(pi, rd, N), Q = rr_player(N - 1 - pi, rd, N);
+          if (P > Q) { int t_ = P; P = Q; Q = t_; }
+          const bool onU = ch >= nch;
+          cplx<T>* M = onU ? Ut : X;
+          const int ld = onU ? r : ldx, ncol = onU ? r : c;
+          const int c0 = (onU ? ch - nch : ch) * JCW, c1 = min(ncol, c0 + JCW);
+          for (int e = tid; e < JP * JP; e += blockDim.x) {
+            // Js[i][k] = (J^H)[i][k] = conj(J[k][i])  or  (J^T)[i][k] = J[k][i]
+            const int i = e / JP, k = e % JP;
+            const cplx<T> v = ldcg(&Jbuf[(size_t)pi * JP * JP + k * JP + i]);
+            Js[i * LD + k] = onU ? v : cconj<T>(v);
+          }
+          int orow[4];
+#pragma unroll
+          for (int a_ = 0; a_ < 4; ++a_) {
+            const int i = 4 * ty + a_;
+            orow[a_] = i < JB ? P * JB + i : Q * JB + (i - JB);
+          }
+          const int nsub = (c1 - c0 + GW - 1) / GW;
+          for (int s = 0; s < nsub; ++s, ++jseq) {
+            cp_async_wait<BJ_NB - 1>();
+            __syncthreads();                    // the stage (and, first time, Js) is visible
+            const cplx<T>* tile = ring + (jseq % BJ_NB) * JP * TS;
+            cplx<T> acc[4][NBC];
+#pragma unroll
+            for (int a_ = 0; a_ < 4; ++a_)
+#pragma unroll
+              for (int b_ = 0; b_ < NBC; ++b_) acc[a_][b_] = czero<T>();
+#pragma unroll 4
+            for (int k = 0; k < JP; ++k) {
+              cplx<T> jv[4], xv[NBC];
+#pragma unroll
+              for (int a_ = 0; a_ < 4; ++a_) jv[a_] = Js[(4 * ty + a_) * LD + k];
+#pragma unroll
+              for (int b_ = 0; b_ < NBC; ++b_) xv[b_] = tile[k * TS + tx + 32 * b_];
+#pragma unroll
+              for (int a_ = 0; a_ < 4; ++a_)
+#pragma unroll
+                for (int b_ = 0; b_ < NBC; ++b_) cfma<T>(acc[a_][b_], jv[a_], xv[b_]);
+            }
+            const int k0 = c0 + s * GW;
+#pragma unroll
+            for (int a_ = 0; a_ < 4; ++a_) {
+              if (orow[a_] >= r) continue;
+#pragma unroll
+              for (int b_ = 0; b_ < NBC; ++b_) {
+                const int col = k0 + tx + 32 * b_;
+                if (col < c1) stcg(&M[(size_t)orow[a_] * ld + col], acc[a_][b_]);
+              }
+            }
+            __syncthreads();                    // stage consumed: refill it
+            issue(jseq % BJ_NB);
+            cp_async_commit();
           }
         }
+        cp_async_wait<0>();
         __syncthreads();
       }
       if (!grid_barrier(&ctl->g, nblk, timeout_ns)) return;

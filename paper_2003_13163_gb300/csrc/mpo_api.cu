@@ -43,6 +43,8 @@
 namespace {
 
 thread_local std::string g_last_init_error;
+thread_local int g_last_svd_sweeps = 0;           // statistics of the last mpo_svd on this thread
+thread_local double g_last_svd_phase_ms[3] = {0.0, 0.0, 0.0};
 
 struct HostSync {   // pinned read-back of the last select + eigen-solve
   SelectInfo info;
@@ -77,8 +79,8 @@ struct mpo_ctx {
   GridCtl* ctl = nullptr;
   OSCtl* osctl = nullptr;          // control block of the Jacobi launches (barriers, status, counts)
   void *bj_gpart = nullptr, *bj_j = nullptr;   // block Jacobi partial Grams and pair rotations
-  int* bj_act = nullptr;
-  size_t bj_slots = 0;
+  int* bj_act = nullptr;                        // block Jacobi integer state (bj_state_ints)
+  size_t bj_slots = 0, bj_act_ints = 0;
   int block_min_rows = 0;
   bool tensor_cores = false;       // FP32 plain products on tcgen05
   int* tc_status = nullptr;        // set by the tensor-core GEMM if a wait timed out
@@ -107,8 +109,8 @@ struct mpo_ctx {
   double prof_phase_ns[3] = {0, 0, 0};
 };
 
-enum { PK_SVD = 0, PK_GEMM, PK_SUPEROP, PK_SELECT, PK_GATHER, PK_TRANSPOSE, PK_TRACE, PK_TCGEMM, PK_NCLASS };
-static const char* kProfNames[PK_NCLASS] = {"svd_jacobi", "cgemm", "superop", "select", "gather", "transpose", "trace",
+enum { PK_SVD = 0, PK_SVD_SWEEP, PK_GEMM, PK_SUPEROP, PK_SELECT, PK_GATHER, PK_TRANSPOSE, PK_TRACE, PK_TCGEMM, PK_NCLASS };
+static const char* kProfNames[PK_NCLASS] = {"svd_gate", "svd_sweep", "cgemm", "superop", "select", "gather", "transpose", "trace",
                                             "tc_cgemm"};
 
 static cudaEvent_t prof_event(mpo_ctx* h) {
@@ -243,8 +245,8 @@ static cudaError_t launch_onesided(cudaStream_t st, cplx<T>* X, int r, int c, in
 
 template <typename T>
 static cudaError_t launch_block_jacobi(cudaStream_t st, cplx<T>* X, int r, int c, int ldx, cplx<T>* Ut, T* w,
-                                      cplx<T>* Gpart, size_t gpart_slots, cplx<T>* Jbuf, int* act, OSCtl* ctl,
-                                      int max_sweeps, double timeout_s, int num_sms) {
+                                      cplx<T>* Gpart, size_t gpart_slots, cplx<T>* Jbuf, int* act, size_t act_ints,
+                                      OSCtl* ctl, int max_sweeps, double timeout_s, int num_sms) {
   const int smem = block_jacobi_smem_bytes<T>();
   cudaError_t e = cudaFuncSetAttribute(block_jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
@@ -254,7 +256,7 @@ static cudaError_t launch_block_jacobi(cudaStream_t st, cplx<T>* X, int r, int c
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int nb = (r + JB - 1) / JB, npairs = (nb + (nb & 1)) / 2;
   const size_t nch = (size_t)(c + JCW - 1) / JCW;
-  if ((size_t)npairs * nch > gpart_slots) return cudaErrorInvalidValue;   // workspace too small
+  if ((size_t)npairs * nch > gpart_slots || bj_state_ints(r) > act_ints) return cudaErrorInvalidValue;   // workspace too small
   const int items = npairs * ((c + JCW - 1) / JCW + (r + JCW - 1) / JCW);
   const int blocks = std::max(1, std::min(per_sm * num_sms, items));
   e = cudaMemsetAsync(ctl, 0, sizeof(OSCtl), st);
@@ -281,11 +283,11 @@ static int svd_select(mpo_ctx* h, cplx<T>* X, int r, int c, int ldx, int cap, bo
     // (4 mn^2 mx real flops) plus its dense eigen-decomposition (13.3 mn^3);
     // bytes: read and write X, write U
     const double mn = std::min(r, c), mx = std::max(r, c);
-    ProfScope ps(h, PK_SVD, 4.0 * mn * mn * mx + 13.3 * mn * mn * mn,
+    ProfScope ps(h, disc ? PK_SVD : PK_SVD_SWEEP, 4.0 * mn * mn * mx + 13.3 * mn * mn * mn,
                  (2.0 * r * c + (double)r * r) * sizeof(cplx<T>));
     if (h->block_min_rows > 0 && r >= h->block_min_rows)
       CK(h, launch_block_jacobi<T>(h->st, X, r, c, ldx, (cplx<T>*)h->vecs, w, (cplx<T>*)h->bj_gpart, h->bj_slots,
-                                   (cplx<T>*)h->bj_j, h->bj_act, h->osctl, h->opts.eig_max_sweeps,
+                                   (cplx<T>*)h->bj_j, h->bj_act, h->bj_act_ints, h->osctl, h->opts.eig_max_sweeps,
                                    h->opts.barrier_timeout_s, h->num_sms));
     else
       CK(h, launch_onesided<T>(h->st, X, r, c, ldx, (cplx<T>*)h->vecs, w, h->osctl, h->opts.eig_max_sweeps,
@@ -730,7 +732,8 @@ int mpo_init(mpo_handle* out, int n, int chi_max, mpo_precision prec, void* stre
     h->bj_slots = bj_pairs * bj_nch;
     ok = ok && alloc(&h->bj_gpart, h->bj_slots * JP * JP * h->esz);
     ok = ok && alloc(&h->bj_j, bj_pairs * JP * JP * h->esz);
-    ok = ok && alloc((void**)&h->bj_act, bj_pairs * sizeof(int));
+    h->bj_act_ints = bj_state_ints(m);
+    ok = ok && alloc((void**)&h->bj_act, h->bj_act_ints * sizeof(int));
   }
   ok = ok && alloc((void**)&h->scal, 4 * sizeof(double));
   ok = ok && alloc((void**)&h->dS, (size_t)(n - 1) * sizeof(double));
@@ -994,6 +997,12 @@ int mpo_to_dense(mpo_handle h, double* rho_vec) {
   return MPO_OK;
 }
 
+int mpo_svd_last_stats(int* sweeps, double* phase_ms3) {
+  if (sweeps) *sweeps = g_last_svd_sweeps;
+  if (phase_ms3) for (int i = 0; i < 3; ++i) phase_ms3[i] = g_last_svd_phase_ms[i];
+  return MPO_OK;
+}
+
 int mpo_svd(int r, int c, void* X, void* w, void* Ut, mpo_precision prec, int max_sweeps, int block, void* stream) {
   if (r < 1 || c < 1 || !X || !w || !Ut) return MPO_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
@@ -1009,7 +1018,7 @@ int mpo_svd(int r, int c, void* X, void* w, void* Ut, mpo_precision prec, int ma
   if (block) {
     ok = ok && cudaMalloc(&gp, pairs * nch * JP * JP * esz) == cudaSuccess;
     ok = ok && cudaMalloc(&jb, pairs * JP * JP * esz) == cudaSuccess;
-    ok = ok && cudaMalloc((void**)&act, pairs * sizeof(int)) == cudaSuccess;
+    ok = ok && cudaMalloc((void**)&act, bj_state_ints(r) * sizeof(int)) == cudaSuccess;
   }
   if (!ok) { cudaGetLastError(); cudaFree(ctl); cudaFree(gp); cudaFree(jb); cudaFree(act); return MPO_ERR_OOM; }
   const int ms = max_sweeps > 0 ? max_sweeps : 40;
@@ -1017,18 +1026,21 @@ int mpo_svd(int r, int c, void* X, void* w, void* Ut, mpo_precision prec, int ma
   if (block)
     e = prec == MPO_FP64
         ? launch_block_jacobi<double>(st, (double2*)X, r, c, c, (double2*)Ut, (double*)w, (double2*)gp, pairs * nch,
-                                      (double2*)jb, act, ctl, ms, 5.0, sms)
+                                      (double2*)jb, act, bj_state_ints(r), ctl, ms, 5.0, sms)
         : launch_block_jacobi<float>(st, (float2*)X, r, c, c, (float2*)Ut, (float*)w, (float2*)gp, pairs * nch,
-                                     (float2*)jb, act, ctl, ms, 5.0, sms);
+                                     (float2*)jb, act, bj_state_ints(r), ctl, ms, 5.0, sms);
   else
     e = prec == MPO_FP64
         ? launch_onesided<double>(st, (double2*)X, r, c, c, (double2*)Ut, (double*)w, ctl, ms, 5.0, sms)
         : launch_onesided<float>(st, (float2*)X, r, c, c, (float2*)Ut, (float*)w, ctl, ms, 5.0, sms);
-  GridCtl hc{};
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, &ctl->g, sizeof(GridCtl), cudaMemcpyDeviceToHost, st);
+  OSCtl hctl{};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hctl, ctl, sizeof(OSCtl), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(ctl); cudaFree(gp); cudaFree(jb); cudaFree(act);
   if (e != cudaSuccess) { g_last_init_error = cudaGetErrorString(e); return MPO_ERR_CUDA; }
+  const GridCtl& hc = hctl.g;
+  g_last_svd_sweeps = hc.sweeps;
+  for (int i = 0; i < 3; ++i) g_last_svd_phase_ms[i] = block ? 1e-6 * (double)hctl.phase_ns[i] : 0.0;
   if (hc.err) return MPO_ERR_TIMEOUT;
   if (hc.status) return MPO_ERR_NOCONV;
   return MPO_OK;
@@ -1054,7 +1066,7 @@ constexpr size_t kStaticChunks = (size_t)((kStaticMaxCols + JCW - 1) / JCW + 1);
 constexpr size_t kStaticSlots = kStaticPairs * kStaticChunks;
 struct StaticSvdScratch {       // laid out for the widest element (complex128)
   OSCtl ctl;
-  int act[kStaticPairs];
+  int act[bj_state_ints(kStaticMaxRows)];
   double2 jbuf[kStaticPairs * JP * JP];
   double2 gpart[kStaticSlots * JP * JP];
 };
@@ -1102,13 +1114,16 @@ int mpo_svd_static(int r, int c, void* X, void* w, void* Ut, mpo_precision prec,
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int ms = max_sweeps > 0 ? max_sweeps : 40;
   // launch_block_jacobi clears the control block (barrier counters, status,
-  // per-sweep counts) before the launch; the Gram partials, rotations and
-  // pair flags are fully written before they are read in every round
+  // per-sweep counts) before the launch; the kernel clears its round stamps
+  // first, and the Gram partials, rotations and pair flags are fully written
+  // before they are read in every round
   cudaError_t e = prec == MPO_FP64
       ? launch_block_jacobi<double>(st, (double2*)X, r, c, c, (double2*)Ut, (double*)w, (double2*)s->gpart,
-                                    kStaticSlots, (double2*)s->jbuf, s->act, &s->ctl, ms, 5.0, sms)
+                                    kStaticSlots, (double2*)s->jbuf, s->act, bj_state_ints(kStaticMaxRows), &s->ctl,
+                                    ms, 5.0, sms)
       : launch_block_jacobi<float>(st, (float2*)X, r, c, c, (float2*)Ut, (float*)w, (float2*)s->gpart,
-                                   kStaticSlots, (float2*)s->jbuf, s->act, &s->ctl, ms, 5.0, sms);
+                                   kStaticSlots, (float2*)s->jbuf, s->act, bj_state_ints(kStaticMaxRows), &s->ctl,
+                                   ms, 5.0, sms);
   GridCtl hc{};
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, &s->ctl.g, sizeof(GridCtl), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -21,7 +21,7 @@ EXPORTS = ["mpo_default_opts", "mpo_init", "mpo_apply_layer", "mpo_apply_gate", 
            "mpo_entropy", "mpo_schmidt", "mpo_bond_dims", "mpo_get_site", "mpo_to_dense", "mpo_centre",
            "mpo_device_bytes", "mpo_free", "mpo_last_error", "mpo_eigh", "mpo_svd", "mpo_version",
            "mpo_profile", "mpo_profile_read", "mpo_profile_sweeps", "mpo_profile_phases", "mpo_svd_static",
-           "mpo_probability", "mpo_sample", "mpo_gemm"]
+           "mpo_probability", "mpo_sample", "mpo_gemm", "mpo_svd_last_stats"]
 
 
 class MPOError(RuntimeError):
@@ -78,6 +78,7 @@ def load_library(path: str | None = None):
         "mpo_probability": (I, [P, I, P, P]),
         "mpo_sample": (I, [P, I, P, P, P]),
         "mpo_gemm": (I, [I, I, I, P, P, P, I, I, P]),
+        "mpo_svd_last_stats": (I, [IP, DP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -297,6 +298,16 @@ def svd_rows(X, precision: str = "fp64", max_sweeps: int = 0, block: bool = Fals
     if rc != 0:
         raise MPOError(rc, "mpo_svd failed")
     return w, Ut
+
+
+def svd_last_stats() -> dict:
+    """Sweeps and block-Jacobi phase times (ms) of the last svd_rows call on
+    this thread."""
+    lib = load_library()
+    sw = ctypes.c_int()
+    ph = (ctypes.c_double * 3)()
+    lib.mpo_svd_last_stats(ctypes.byref(sw), ph)
+    return {"sweeps": sw.value, "gram_ms": ph[0], "pair_eig_ms": ph[1], "apply_ms": ph[2]}
 
 
 def svd_rows_static(X, precision: str = "fp64", max_sweeps: int = 0):

@@ -38,7 +38,10 @@ def main(argv):
             t = time.time()
             mpo.svd_rows(X, prec, block=block)
             torch.cuda.synchronize()
-            print(f"svd {prec} {r}x{c} block={block}: {time.time() - t:.4f} s", flush=True)
+            el = time.time() - t
+            st = mpo.svd_last_stats()
+            print(f"svd {prec} {r}x{c} block={block}: {el:.4f} s, {st['sweeps']} sweeps, phases G/E/A "
+                  f"{st['gram_ms']:.1f}/{st['pair_eig_ms']:.1f}/{st['apply_ms']:.1f} ms", flush=True)
     elif what == "gemm":
         m, n, kk, reps = int(argv[1]), int(argv[2]), int(argv[3]), int(argv[4])
         tc = (argv[5] if len(argv) > 5 else "tc") == "tc"
