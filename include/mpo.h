@@ -170,6 +170,43 @@ int mpo_probability(mpo_handle h, int n_strings, const unsigned char *bits, doub
  * Synchronises the stream; allocates its scratch per call. */
 int mpo_sample(mpo_handle h, int n_samples, const double *uniforms, unsigned char *bits, double *P);
 
+/* ---- Batching form -------------------------------------------------------
+ * k independent circuits (the ensembles of circuit instances the paper runs
+ * per (n, p) point, Sec. 4) held and advanced together. Each instance is an
+ * engine context of its own (n_i qubits, the shared chi_max, precision and
+ * options) on a stream the library creates; n_workers host threads (<= 0:
+ * min(8, k)) drive the instances of a call concurrently, longest chains
+ * first. A batch handle accepts only the calls of this block, mpo_free and
+ * mpo_last_error; the other calls return MPO_ERR_ARG on it.
+ *   n_i        : host [k], each even, 2..4096.
+ *   cuda_stream: the caller's stream; each call's work starts after the work
+ *                already queued on it (so device gate arrays written there
+ *                are safe to read).
+ * Errors as mpo_init; the message names the failing instance. */
+int mpo_init_batch(mpo_handle *out, int k, const int *n_i, int chi_max, mpo_precision prec, void *cuda_stream,
+                   const mpo_opts *opts, int n_workers);
+
+/* One step t (1-based; odd t acts on paper bonds 1, 3, ..., even t on 2, 4,
+ * ..., in ascending order, Sec. 3.3) on every instance i with active[i] != 0
+ * (active NULL: all). Synchronous: returns when every instance has finished.
+ *   gates_all : host or device; for each active instance in index order, its
+ *               (n_i - parity) / 2 gates as [4][4] complex128 (row-major,
+ *               interleaved), where parity = (t + 1) % 2;
+ *   p_all     : host [k], the paper's p of each instance (one per instance);
+ *   S_all     : nullable host out, the n_i - 1 bond entropies (bits) of
+ *               instance i at offset sum_{j<i} (n_j - 1), as mpo_entropy;
+ *   trace_all : nullable host [k] out, Tr rho of each active instance;
+ *   discarded_all: nullable host [k] out, the step's summed discarded weight.
+ * Outputs of inactive instances are left untouched. On an instance's error
+ * the call returns its code and the batch handle enters the error state. */
+int mpo_apply_layer_batch(mpo_handle h, int t, const double *gates_all, const double *p_all, const int *active,
+                          double *S_all, double *trace_all, double *discarded_all);
+
+/* The context of instance i of a batch (owned by the batch: do not free),
+ * for the diagnostic calls (mpo_schmidt, mpo_to_dense, mpo_bond_dims, ...).
+ * Do not use it while mpo_apply_layer_batch runs. */
+int mpo_batch_instance(mpo_handle h, int i, mpo_handle *inst);
+
 /* Contract the MPO into |rho>> (4^n complex128, interleaved, index
  * I_1 I_2 .. I_n with I_1 most significant). n <= 12. Test export. */
 int mpo_to_dense(mpo_handle h, double *rho_vec);

@@ -49,7 +49,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     os.makedirs(LIBDIR, exist_ok=True)
     tmp = LIB + ".tmp"
-    cmd = [nvcc_path(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
+    cmd = [nvcc_path(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread",
            "-I", os.path.join(ROOT, "include"), "-o", tmp, os.path.join(CSRC, "mpo_api.cu")]
     if verbose:
         print(" ".join(cmd), flush=True)

@@ -89,6 +89,22 @@ def random_circuit(n: int, depth: int, p: float, seed: int) -> Circuit:
     return c
 
 
+def ensemble_instances(k: int, seed: int = 4, n_choices=(16, 24, 32, 40, 48, 56, 64),
+                       p_choices=(0.005, 0.01, 0.02, 0.05), depth_per_qubit: int = 2,
+                       gate_seed0: int = 1000) -> list[Circuit]:
+    """k independent instances for the batching form: (n_i, p_i) drawn
+    uniformly from the choices with PCG64(seed) (n first, then p, per
+    instance), depth D_i = depth_per_qubit * n_i, and instance i's gates from
+    PCG64(gate_seed0 + i)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(k):
+        n = int(n_choices[rng.integers(len(n_choices))])
+        p = float(p_choices[rng.integers(len(p_choices))])
+        out.append(random_circuit(n, depth_per_qubit * n, p, gate_seed0 + i))
+    return out
+
+
 def random_hermitian_psd(m: int, decay: float, seed: int, dtype=np.complex128) -> np.ndarray:
     """Seeded Hermitian positive semidefinite m x m matrix with spectrum
     exp(-decay * k), k = 0..m-1 (a test input for the eigensolver; the

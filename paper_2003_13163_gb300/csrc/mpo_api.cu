@@ -33,6 +33,8 @@
 #include <vector>
 #include <algorithm>
 #include <type_traits>
+#include <atomic>
+#include <thread>
 
 #include "../../include/mpo.h"
 #include "common.cuh"
@@ -55,7 +57,10 @@ struct HostSync {   // pinned read-back of the last select + eigen-solve
 
 }  // namespace
 
+struct BatchState;
+
 struct mpo_ctx {
+  BatchState* batch = nullptr;     // set on handles made by mpo_init_batch
   int n = 0, chi_max = 0;
   mpo_precision prec = MPO_FP64;
   cudaStream_t st = nullptr;
@@ -773,8 +778,11 @@ int mpo_init(mpo_handle* out, int n, int chi_max, mpo_precision prec, void* stre
   return MPO_OK;
 }
 
+static void batch_free(mpo_ctx* h);
+
 void mpo_free(mpo_handle h) {
   if (!h) return;
+  if (h->batch) { batch_free(h); return; }
   for (void* p : h->site) if (p) cudaFree(p);
   void* ps[] = {h->spare, h->theta, h->theta2, h->osctl, h->tc_status, h->bj_gpart, h->bj_j, h->bj_act, h->vecs, h->tmp, h->wv, h->perm, h->lam2, h->Ms, h->dgates,
                 h->dsup, h->dp, h->info, h->ctl, h->scal, h->dS, h->dschmidt, h->tv0, h->tv1};
@@ -790,11 +798,15 @@ const char* mpo_last_error(mpo_handle h) {
   return h->msg.c_str();
 }
 
-#define GUARD(h)                                      \
-  do {                                                \
-    if (!(h)) return MPO_ERR_ARG;                     \
-    if ((h)->failed) return MPO_ERR_STATE;            \
-    cudaSetDevice((h)->device);                       \
+#define GUARD(h)                                                        \
+  do {                                                                  \
+    if (!(h)) return MPO_ERR_ARG;                                       \
+    if ((h)->batch) {                                                   \
+      (h)->msg = "a batch handle takes only the batch calls";           \
+      return MPO_ERR_ARG;                                               \
+    }                                                                   \
+    if ((h)->failed) return MPO_ERR_STATE;                              \
+    cudaSetDevice((h)->device);                                         \
   } while (0)
 
 int mpo_apply_layer(mpo_handle h, int parity, const double* gates, const double* p, int p_stride) {
@@ -1177,6 +1189,157 @@ int mpo_eigh(int m, void* A, void* w, void* V, mpo_precision prec, int max_sweep
   if (e != cudaSuccess) { g_last_init_error = cudaGetErrorString(e); return MPO_ERR_CUDA; }
   if (hc.err) return MPO_ERR_TIMEOUT;
   if (hc.status) return MPO_ERR_NOCONV;
+  return MPO_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Batching form: k independent circuits (the paper's ensembles of circuit
+// instances per (n, p) point, Sec. 4) advanced one step per call. Every
+// instance is an ordinary engine context on a stream of its own; a call hands
+// the instances to n_workers host threads, longest chains first, each thread
+// driving its instances' layers (whose Jacobi factorisations wait on the host
+// for the kept rank) while the others keep the GPU busy with theirs.
+// ---------------------------------------------------------------------------
+struct BatchState {
+  std::vector<mpo_ctx*> inst;
+  std::vector<cudaStream_t> streams;
+  std::vector<int> n_i, order;     // order: instance indices by decreasing n
+  std::vector<size_t> s_off;       // offset of instance i's n_i - 1 entropies
+  int workers = 1;
+  cudaStream_t caller = nullptr;
+  cudaEvent_t ready = nullptr;
+};
+
+static void batch_free(mpo_ctx* h) {
+  BatchState* B = h->batch;
+  cudaSetDevice(h->device);
+  for (mpo_ctx* q : B->inst) mpo_free(q);
+  for (cudaStream_t s : B->streams) if (s) cudaStreamDestroy(s);
+  if (B->ready) cudaEventDestroy(B->ready);
+  delete B;
+  delete h;
+}
+
+int mpo_init_batch(mpo_handle* out, int k, const int* n_i, int chi_max, mpo_precision prec, void* stream,
+                   const mpo_opts* opts, int n_workers) {
+  if (!out) { g_last_init_error = "out is NULL"; return MPO_ERR_ARG; }
+  *out = nullptr;
+  if (k < 1 || !n_i) { g_last_init_error = "k must be >= 1 and n_i non-NULL"; return MPO_ERR_ARG; }
+  for (int i = 0; i < k; ++i)
+    if (n_i[i] < 2 || n_i[i] % 2 || n_i[i] > 4096) {
+      g_last_init_error = "n_i[" + std::to_string(i) + "] must be even, 2..4096";
+      return MPO_ERR_ARG;
+    }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    g_last_init_error = "no CUDA device";
+    return MPO_ERR_CUDA;
+  }
+  mpo_ctx* h = new mpo_ctx();
+  h->batch = new BatchState();
+  BatchState& B = *h->batch;
+  h->chi_max = chi_max;
+  h->prec = prec;
+  cudaGetDevice(&h->device);
+  B.caller = (cudaStream_t)stream;
+  B.workers = std::max(1, std::min(n_workers > 0 ? n_workers : 8, k));
+  if (cudaEventCreateWithFlags(&B.ready, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    batch_free(h);
+    g_last_init_error = "cudaEventCreate failed";
+    return MPO_ERR_CUDA;
+  }
+  size_t off = 0;
+  for (int i = 0; i < k; ++i) {
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      batch_free(h);
+      g_last_init_error = "cudaStreamCreate failed";
+      return MPO_ERR_CUDA;
+    }
+    B.streams.push_back(s);
+    mpo_handle q = nullptr;
+    const int rc = mpo_init(&q, n_i[i], chi_max, prec, s, opts);
+    if (rc) {
+      const std::string m = "instance " + std::to_string(i) + ": " + g_last_init_error;
+      batch_free(h);
+      g_last_init_error = m;
+      return rc;
+    }
+    B.inst.push_back(q);
+    B.n_i.push_back(n_i[i]);
+    B.s_off.push_back(off);
+    off += (size_t)(n_i[i] - 1);
+  }
+  B.order.resize(k);
+  for (int i = 0; i < k; ++i) B.order[i] = i;
+  std::stable_sort(B.order.begin(), B.order.end(), [&](int x, int y) { return B.n_i[x] > B.n_i[y]; });
+  *out = h;
+  return MPO_OK;
+}
+
+int mpo_apply_layer_batch(mpo_handle h, int t, const double* gates_all, const double* p_all, const int* active,
+                          double* S_all, double* trace_all, double* discarded_all) {
+  if (!h || !h->batch) return MPO_ERR_ARG;
+  if (h->failed) return MPO_ERR_STATE;
+  if (t < 1 || !p_all) { h->msg = "t must be >= 1 and p_all non-NULL"; return MPO_ERR_ARG; }
+  BatchState& B = *h->batch;
+  const int k = (int)B.inst.size();
+  const int parity = (t % 2 == 1) ? 0 : 1;   // odd steps: paper bonds 1, 3, ...; even steps: 2, 4, ...
+  std::vector<size_t> goff(k, 0);
+  size_t acc = 0;
+  for (int i = 0; i < k; ++i) {
+    if (active && !active[i]) continue;
+    goff[i] = acc;
+    acc += (size_t)((B.n_i[i] - parity) / 2) * 32;   // gates x 4 x 4 complex128
+  }
+  if (acc > 0 && !gates_all) { h->msg = "gates_all is NULL"; return MPO_ERR_ARG; }
+  cudaSetDevice(h->device);
+  if (cudaEventRecord(B.ready, B.caller) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, MPO_ERR_CUDA, "cudaEventRecord on the caller's stream failed");
+  }
+  std::atomic<int> next{0};
+  std::vector<int> rcs(k, MPO_OK);
+  auto work = [&]() {
+    cudaSetDevice(h->device);
+    std::vector<double> scratch;
+    for (;;) {
+      const int j = next.fetch_add(1);
+      if (j >= k) break;
+      const int i = B.order[j];
+      if (active && !active[i]) continue;
+      mpo_ctx* q = B.inst[i];
+      if (cudaStreamWaitEvent(q->st, B.ready, 0) != cudaSuccess) { cudaGetLastError(); rcs[i] = MPO_ERR_CUDA; continue; }
+      int rc = mpo_apply_layer(q, parity, gates_all + goff[i], p_all + i, 0);
+      if (rc == MPO_OK && (S_all || trace_all || discarded_all)) {
+        scratch.resize(B.n_i[i] - 1);
+        double tr = 0.0, dw = 0.0;
+        rc = mpo_entropy(q, S_all ? S_all + B.s_off[i] : scratch.data(), trace_all ? &tr : nullptr, &dw);
+        if (rc == MPO_OK) {
+          if (trace_all) trace_all[i] = tr;
+          if (discarded_all) discarded_all[i] = dw;
+        }
+      }
+      rcs[i] = rc;
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int w = 1; w < B.workers; ++w) pool.emplace_back(work);
+  work();
+  for (auto& th : pool) th.join();
+  for (int i = 0; i < k; ++i)
+    if (rcs[i] != MPO_OK) return fail(h, rcs[i], "instance " + std::to_string(i) + ": " + B.inst[i]->msg);
+  return MPO_OK;
+}
+
+int mpo_batch_instance(mpo_handle h, int i, mpo_handle* inst) {
+  if (!h || !h->batch || !inst) return MPO_ERR_ARG;
+  if (i < 0 || i >= (int)h->batch->inst.size()) { h->msg = "instance index out of range"; return MPO_ERR_ARG; }
+  *inst = h->batch->inst[i];
   return MPO_OK;
 }
 

@@ -21,7 +21,8 @@ EXPORTS = ["mpo_default_opts", "mpo_init", "mpo_apply_layer", "mpo_apply_gate", 
            "mpo_entropy", "mpo_schmidt", "mpo_bond_dims", "mpo_get_site", "mpo_to_dense", "mpo_centre",
            "mpo_device_bytes", "mpo_free", "mpo_last_error", "mpo_eigh", "mpo_svd", "mpo_version",
            "mpo_profile", "mpo_profile_read", "mpo_profile_sweeps", "mpo_profile_phases", "mpo_svd_static",
-           "mpo_probability", "mpo_sample", "mpo_gemm", "mpo_svd_last_stats"]
+           "mpo_probability", "mpo_sample", "mpo_gemm", "mpo_svd_last_stats",
+           "mpo_init_batch", "mpo_apply_layer_batch", "mpo_batch_instance"]
 
 
 class MPOError(RuntimeError):
@@ -79,6 +80,9 @@ def load_library(path: str | None = None):
         "mpo_sample": (I, [P, I, P, P, P]),
         "mpo_gemm": (I, [I, I, I, P, P, P, I, I, P]),
         "mpo_svd_last_stats": (I, [IP, DP]),
+        "mpo_init_batch": (I, [ctypes.POINTER(P), I, IP, I, I, P, ctypes.POINTER(Opts), I]),
+        "mpo_apply_layer_batch": (I, [P, I, P, DP, IP, DP, DP, DP]),
+        "mpo_batch_instance": (I, [P, I, ctypes.POINTER(P)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -111,28 +115,39 @@ def default_opts() -> Opts:
     return o
 
 
+def _make_opts(cutoff=0.0, eig_max_sweeps=0, arena_cap_bytes=0, centre_only=False, barrier_timeout_s=0.0,
+               block_jacobi_min_rows=0, tensor_cores=False) -> Opts:
+    o = default_opts()
+    if cutoff > 0:
+        o.sv_rel_cutoff = cutoff
+    if eig_max_sweeps > 0:
+        o.eig_max_sweeps = eig_max_sweeps
+    o.arena_cap_bytes = arena_cap_bytes
+    o.smode = MPO_S_CENTRE if centre_only else MPO_S_ALL_BONDS
+    if barrier_timeout_s > 0:
+        o.barrier_timeout_s = barrier_timeout_s
+    o.block_jacobi_min_rows = block_jacobi_min_rows
+    o.tensor_cores = 1 if tensor_cores else 0
+    return o
+
+
 class MPO:
     """Handle on one device-resident MPO (see include/mpo.h)."""
 
     def __init__(self, n: int, chi_max: int, precision: str = "fp64", *, cutoff: float = 0.0,
                  eig_max_sweeps: int = 0, arena_cap_bytes: int = 0, centre_only: bool = False,
                  barrier_timeout_s: float = 0.0, block_jacobi_min_rows: int = 0, tensor_cores: bool = False,
-                 stream=None):
+                 stream=None, _borrowed=None):
         lib = load_library()
         self._lib = lib
         self.n, self.chi_max = n, chi_max
         self.prec = {"fp64": MPO_FP64, "fp32": MPO_FP32}[precision]
-        o = default_opts()
-        if cutoff > 0:
-            o.sv_rel_cutoff = cutoff
-        if eig_max_sweeps > 0:
-            o.eig_max_sweeps = eig_max_sweeps
-        o.arena_cap_bytes = arena_cap_bytes
-        o.smode = MPO_S_CENTRE if centre_only else MPO_S_ALL_BONDS
-        if barrier_timeout_s > 0:
-            o.barrier_timeout_s = barrier_timeout_s
-        o.block_jacobi_min_rows = block_jacobi_min_rows
-        o.tensor_cores = 1 if tensor_cores else 0
+        self._owned = _borrowed is None
+        if _borrowed is not None:        # an instance of a batch: the batch owns it
+            self.h = _borrowed
+            return
+        o = _make_opts(cutoff, eig_max_sweeps, arena_cap_bytes, centre_only, barrier_timeout_s,
+                       block_jacobi_min_rows, tensor_cores)
         h = ctypes.c_void_p()
         st = ctypes.c_void_p(stream) if stream is not None else _current_stream()
         rc = lib.mpo_init(ctypes.byref(h), n, chi_max, self.prec, st, ctypes.byref(o))
@@ -247,9 +262,9 @@ class MPO:
         return int(self._lib.mpo_device_bytes(self.h))
 
     def close(self) -> None:
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and getattr(self, "_owned", True):
             self._lib.mpo_free(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
@@ -263,6 +278,75 @@ class MPO:
     def __exit__(self, *a):
         self.close()
 
+
+
+class MPOBatch:
+    """k independent circuits held and advanced together (the batching form,
+    see mpo_init_batch in include/mpo.h)."""
+
+    def __init__(self, n_list, chi_max: int, precision: str = "fp32", *, workers: int = 0, stream=None, **opts):
+        lib = load_library()
+        self._lib = lib
+        self.n_list = [int(n) for n in n_list]
+        self.k = len(self.n_list)
+        self.chi_max = chi_max
+        self.precision = precision
+        self.prec = {"fp64": MPO_FP64, "fp32": MPO_FP32}[precision]
+        self.offsets = np.concatenate([[0], np.cumsum([n - 1 for n in self.n_list])]).astype(np.int64)
+        o = _make_opts(**opts)
+        nn = np.ascontiguousarray(self.n_list, dtype=np.int32)
+        h = ctypes.c_void_p()
+        st = ctypes.c_void_p(stream) if stream is not None else _current_stream()
+        rc = lib.mpo_init_batch(ctypes.byref(h), self.k, nn.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                chi_max, self.prec, st, ctypes.byref(o), int(workers))
+        if rc != 0:
+            raise MPOError(rc, lib.mpo_last_error(None).decode())
+        self.h = h
+
+    def _check(self, rc):
+        if rc != 0:
+            raise MPOError(rc, self._lib.mpo_last_error(self.h).decode())
+
+    def apply_layer(self, t: int, gates, p, active=None, *, with_trace: bool = True):
+        """Step t (1-based) on the active instances. gates: list over the
+        active instances (index order) of (n_gates, 4, 4) complex arrays, or
+        one concatenated complex128 array; p: (k,) rates. Returns (S list of
+        per-instance entropy arrays, trace (k,), discarded (k,)); entries of
+        inactive instances are NaN."""
+        if isinstance(gates, (list, tuple)):
+            gates = (np.concatenate([np.asarray(g, dtype=np.complex128).reshape(-1) for g in gates])
+                     if len(gates) else np.zeros(0, dtype=np.complex128))
+        if isinstance(gates, np.ndarray):
+            gates = np.ascontiguousarray(gates, dtype=np.complex128)
+        pa = np.ascontiguousarray(np.broadcast_to(np.asarray(p, dtype=np.float64), (self.k,)))
+        act = None if active is None else np.ascontiguousarray(active, dtype=np.int32)
+        S = np.full(int(self.offsets[-1]), np.nan)
+        tr = np.full(self.k, np.nan)
+        dw = np.full(self.k, np.nan)
+        DP = ctypes.POINTER(ctypes.c_double)
+        self._check(self._lib.mpo_apply_layer_batch(
+            self.h, int(t), _ptr(gates) if (gates.size if isinstance(gates, np.ndarray) else gates.numel()) else None,
+            pa.ctypes.data_as(DP),
+            None if act is None else act.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+            S.ctypes.data_as(DP), tr.ctypes.data_as(DP) if with_trace else None, dw.ctypes.data_as(DP)))
+        return [S[self.offsets[i]:self.offsets[i + 1]] for i in range(self.k)], tr, dw
+
+    def instance(self, i: int) -> "MPO":
+        """The instance's context for diagnostics (owned by the batch)."""
+        q = ctypes.c_void_p()
+        self._check(self._lib.mpo_batch_instance(self.h, int(i), ctypes.byref(q)))
+        return MPO(self.n_list[i], self.chi_max, self.precision, _borrowed=q)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self._lib.mpo_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 def eigh(A, precision: str = "fp64", max_sweeps: int = 0):
     """Hermitian eigen-solve on the device through the C ABI (test export).

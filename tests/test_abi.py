@@ -44,6 +44,13 @@ def test_argument_validation_before_device(lib):
     assert lib.mpo_init(ctypes.byref(h), 8, 16, 5, None, None) == -1     # precision
     assert lib.mpo_init(None, 8, 16, 0, None, None) == -1
     assert lib.mpo_apply_layer(None, 0, None, None, 0) == -1
+    n_i = (ctypes.c_int * 2)(8, 7)
+    assert lib.mpo_init_batch(None, 2, n_i, 16, 0, None, None, 0) == -1
+    assert lib.mpo_init_batch(ctypes.byref(h), 0, n_i, 16, 0, None, None, 0) == -1   # k
+    assert lib.mpo_init_batch(ctypes.byref(h), 2, n_i, 16, 0, None, None, 0) == -1   # odd n_1
+    assert lib.mpo_init_batch(ctypes.byref(h), 2, None, 16, 0, None, None, 0) == -1
+    assert lib.mpo_apply_layer_batch(None, 1, None, None, None, None, None, None) == -1
+    assert lib.mpo_batch_instance(None, 0, ctypes.byref(h)) == -1
     lib.mpo_free(None)                                                    # no-op
 
 
@@ -53,6 +60,9 @@ def test_no_cpu_fallback(lib):
         pytest.skip("GPU present")
     with pytest.raises(mpo.MPOError) as e:
         mpo.MPO(8, 16)
+    assert e.value.code == -2
+    with pytest.raises(mpo.MPOError) as e:
+        mpo.MPOBatch([8, 6], 16)
     assert e.value.code == -2
 
 
