@@ -42,6 +42,9 @@ WORKLOADS = {
     "n64_chi1024_p0.005": dict(n=64, chi=1024, p=0.005, seed=2, precision="fp32"),
     "n32_chi256_p0.01": dict(n=32, chi=256, p=0.01, seed=1, precision="fp64"),
     "n8_chi256_p0.02": dict(n=8, chi=256, p=0.02, seed=0, precision="fp64"),
+    # batching form: 256 instances, n_i in {16, 24, ..., 64}, p_i in {.005, .01,
+    # .02, .05} from PCG64(4), D_i = 2 n_i, instance gates from PCG64(1000 + i)
+    "batch256_chi128": dict(n=64, chi=128, p=0.02, seed=4, precision="fp32", batch=256),
 }
 DEFAULT_WORKLOAD = "n64_chi1024_p0.005"
 METRIC = "noisy-gate MPO updates/s at chi=1024 (n=64 Haar brickwork, p=0.005)"
@@ -164,6 +167,105 @@ def run_reference(args, wl) -> None:
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, wl, prec) -> None:
+    """The batching form: every instance of the ensemble advances one step per
+    timed step (mpo_apply_layer_batch); value = gates of all instances / time.
+    The first layers (until chi_max = 128 is reached) and W warm-up layers run
+    untimed."""
+    import torch
+    from paper_2003_13163_gb300 import build as B
+    from paper_2003_13163_gb300 import replicas
+    world, rank, local = replicas.world()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    B.build()
+    from paper_2003_13163_gb300 import mpo
+    from paper_2003_13163_gb300.circuits import ensemble_instances
+
+    k, chi = wl["batch"], wl["chi"]
+    circs = ensemble_instances(k, seed=replicas.rank_seed(wl["seed"], rank))
+    R, K, W = ramp_layers(16, chi), args.steps, args.warmup
+    T = R + W + 2 * K
+    assert T <= min(c.depth for c in circs)
+    p_all = np.array([float(c.p[0][0]) for c in circs])
+    host = []
+    for t in range(1, T + 1):
+        g = np.concatenate([c.gates[t - 1].reshape(-1) for c in circs])
+        host.append(torch.from_numpy(g.view(np.float64).copy()).pin_memory())
+    devg = [h.to(dev) for h in host]
+    stream = torch.cuda.current_stream(dev)
+    b = mpo.MPOBatch([c.n for c in circs], chi, prec, workers=args.workers, stream=stream.cuda_stream)
+    t = 0
+    t_ramp0 = time.perf_counter()
+    for _ in range(R + W):
+        t += 1
+        b.apply_layer(t, devg[t - 1], p_all, with_trace=False)
+    torch.cuda.synchronize()
+    t_ramp = time.perf_counter() - t_ramp0
+
+    def timed(gate_bufs, with_h2d):
+        nonlocal t
+        gates = h2d = d2h = 0
+        replicas.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            t += 1
+            S, _, _ = b.apply_layer(t, gate_bufs[t - 1], p_all, with_trace=False)
+            gates += sum(len(c.gates[t - 1]) for c in circs)
+            if with_h2d:
+                h2d += gate_bufs[t - 1].numel() * 8 + p_all.nbytes
+                d2h += sum(s.nbytes for s in S) + 8 * k
+        e1.record(stream)
+        torch.cuda.synchronize()
+        replicas.barrier()
+        ms = replicas.max_over_ranks(e0.elapsed_time(e1), device=dev)
+        return gates * world / (ms / 1e3), ms, gates, h2d, d2h
+
+    insts = [b.instance(i) for i in range(k)]
+    for q in insts:
+        q.profile(True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    value, ms, gates, _, _ = timed(devg, False)
+    clk = clocks.stop()
+    kern = {}
+    for q in insts:
+        for name, v in q.profile_read().items():
+            if not name.startswith("_") and v["launches"]:
+                d = kern.setdefault(name, {"ms": 0.0, "launches": 0})
+                d["ms"] += v["ms"]
+                d["launches"] += v["launches"]
+        q.profile(False)
+    e2e_value, _, _, h2d, d2h = timed(host, True)
+    line = {"metric": "noisy-gate MPO updates/s, batching form (256 independent circuits, chi=128)",
+            "value": value, "unit": "gates/s", "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "instances": k,
+                       "n_range": [min(c.n for c in circs), max(c.n for c in circs)],
+                       "chi_max": chi, "seed": wl["seed"], "precision": prec, "workers": args.workers,
+                       "parallelism": f"replicas{world}", "ramp_layers": R, "ramp_seconds": round(t_ramp, 2),
+                       "gates_per_step": gates / K, "l2": "per-step working set of all instances exceeds L2"},
+            "clocks": clk, "gpu_launches": int(sum(v["launches"] for v in kern.values())),
+            "kernels": {name: {"ms_summed_over_streams": round(v["ms"], 1), "launches": v["launches"]}
+                        for name, v in kern.items()},
+            "e2e": {"value": e2e_value, "unit": "gates/s", "h2d_bytes_per_step": h2d // K,
+                    "d2h_bytes_per_step": d2h // K}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    b.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -173,12 +275,16 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default=None, choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workers", type=int, default=8, help="host worker threads of the batching form")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl)
         return
     prec = args.precision or wl["precision"]
+    if "batch" in wl:
+        run_batch(args, wl, prec)
+        return
 
     import torch
     from paper_2003_13163_gb300 import replicas

@@ -637,11 +637,12 @@ constexpr int JCW = 512;         // columns per Gram / apply work item
 
 // Integer state of the block Jacobi for r rows: the per-pair rotate flags of
 // a round, then for each block the round stamp of its last rotation, then
-// for each block pair (P, Q) the stamp of the round that last found it
-// orthogonal (N x N, N = the padded block count).
+// for each block a flag "own rows not known orthogonal", then for each block
+// pair (P, Q) the stamp of the round that last found it orthogonal (N x N,
+// N = the padded block count).
 __host__ __device__ constexpr size_t bj_state_ints(int r) {
   return (size_t)(((r + JB - 1) / JB + (((r + JB - 1) / JB) & 1)) / 2) +
-         (size_t)((r + JB - 1) / JB + (((r + JB - 1) / JB) & 1)) +
+         2 * (size_t)((r + JB - 1) / JB + (((r + JB - 1) / JB) & 1)) +
          (size_t)((r + JB - 1) / JB + (((r + JB - 1) / JB) & 1)) * (size_t)((r + JB - 1) / JB + (((r + JB - 1) / JB) & 1));
 }
 
@@ -708,9 +709,11 @@ __device__ __forceinline__ void bj_rot_params(const cplx<TI>* G, int p, int q, T
 // sweep count is capped, because J is re-derived in every outer round and an
 // inexact inner solve only costs outer sweeps. The rounding drift of the
 // accumulated rotations is removed afterwards by bj_polish_unitary. G0 holds
-// the input; G1 is scratch of the same shape; both are overwritten.
+// the input; G1 is scratch of the same shape; both are overwritten. Returns
+// 1 when a sweep found nothing left to rotate (the result is diagonal to the
+// tolerance), 0 when max_sweeps ran out first.
 template <typename TI>
-__device__ void bj_inner_eig(cplx<TI>* G0, cplx<TI>* G1, cplx<TI>* Vs /*JP x JP, ld JP+1*/, double tol,
+__device__ int bj_inner_eig(cplx<TI>* G0, cplx<TI>* G1, cplx<TI>* Vs /*JP x JP, ld JP+1*/, double tol,
                              double floor_abs, int max_sweeps) {
   constexpr int LD = JP + 1, NR = JP / 2;
   static_assert(NR * NR == 256, "one thread per 2 x 2 block");
@@ -777,8 +780,9 @@ __device__ void bj_inner_eig(cplx<TI>* G0, cplx<TI>* G1, cplx<TI>* Vs /*JP x JP,
       any |= __syncthreads_or(sb != TI(0));
       cplx<TI>* t_ = Gc; Gc = Gn; Gn = t_;
     }
-    if (!any) break;
+    if (!any) return 1;
   }
+  return 0;
 }
 
 // One Newton-Schulz step V <- V (3 I - V^H V) / 2 (Higham, Functions of
@@ -923,8 +927,9 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
   // both unchanged since the round that found it orthogonal stays orthogonal,
   // so cross-only sweeps skip its Gram and its test
   int* last_mod = act_flag + npairs;
-  int* last_clean = last_mod + N;
-  for (size_t e = gtid; e < (size_t)N + (size_t)N * N; e += gthreads) last_mod[e] = 0;
+  int* wdirty = last_mod + N;   // 1: the block's own rows were left by an inexact pair solve
+  int* last_clean = wdirty + N;
+  for (size_t e = gtid; e < 2 * (size_t)N + (size_t)N * N; e += gthreads) last_mod[e] = 0;
   for (long i = gwarp; i < r; i += nwarps) {
     T s = T(0);
     for (int j = lane; j < c; j += 32) { const cplx<T> x = ldcg(&X[(size_t)i * ldx + j]); s += x.x * x.x + x.y * x.y; }
@@ -963,11 +968,18 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
       auto pair_dirty = [&](int P_, int Q_) -> bool {
         return __ldcg(&last_clean[(size_t)P_ * N + Q_]) <= max(__ldcg(&last_mod[P_]), __ldcg(&last_mod[Q_]));
       };
+      // a pair forms its full Gram in full sweeps, and whenever one of its
+      // blocks was left by a pair solve that ran out of inner sweeps (its own
+      // rows are then not known to be orthogonal, which cross-only Grams
+      // assume)
+      auto pair_full = [&](int P_, int Q_) -> bool {
+        return full_gram || __ldcg(&wdirty[P_]) != 0 || __ldcg(&wdirty[Q_]) != 0;
+      };
       auto item_valid = [&](long it) -> bool {
         const int pi_ = (int)(it / nch);
         int P_ = rr_player(pi_, rd, N), Q_ = rr_player(N - 1 - pi_, rd, N);
         if (P_ > Q_) { const int t_ = P_; P_ = Q_; Q_ = t_; }
-        return Q_ < nb && (full_gram || pair_dirty(P_, Q_));
+        return Q_ < nb && (pair_full(P_, Q_) || pair_dirty(P_, Q_));
       };
       long p_item = blockIdx.x;   // producer cursor
       int p_sub = 0;
@@ -1002,6 +1014,7 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
         const int pi = (int)(item / nch), ch = (int)(item % nch);
         int P = rr_player(pi, rd, N), Q = rr_player(N - 1 - pi, rd, N);
         if (P > Q) { int t_ = P; P = Q; Q = t_; }
+        const bool fullp = pair_full(P, Q);
         // full: thread (ti, tj) owns G[ti + 16a][tj + 16b];
         // cross: k-slice g = tid / 16 (k = g, g + 16, ...), member m = tid % 16
         // owns C[4 mi + i][4 mj + j], mi = m / 4, mj = m % 4, and the norms of
@@ -1024,7 +1037,7 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
           __syncthreads();
           const cplx<T>* tile = ring + (jseq % BJ_NB) * JP * TS;
           const int kn = min(GW, c1 - (c0 + s * GW));
-          if (full_gram) {
+          if (fullp) {
 #pragma unroll 4
             for (int k = 0; k < kn; ++k) {
               const cplx<T> a0 = tile[ti * TS + k], a1 = tile[(ti + 16) * TS + k];
@@ -1054,7 +1067,7 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
           cp_async_commit();
         }
         cplx<T>* Gp = Gpart + ((size_t)pi * nch + ch) * JP * JP;
-        if (full_gram) {
+        if (fullp) {
 #pragma unroll
           for (int a_ = 0; a_ < 2; ++a_)
 #pragma unroll
@@ -1108,7 +1121,8 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
       for (long pi = blockIdx.x; pi < npairs; pi += nblk) {
         int P = rr_player((int)pi, rd, N), Q = rr_player(N - 1 - (int)pi, rd, N);
         if (P > Q) { int t_ = P; P = Q; Q = t_; }
-        if (Q >= nb || (!full_gram && !pair_dirty(P, Q))) { if (tid == 0) act_flag[pi] = 0; continue; }
+        const bool full_e = Q < nb && pair_full(P, Q);
+        if (Q >= nb || (!full_e && !pair_dirty(P, Q))) { if (tid == 0) act_flag[pi] = 0; continue; }
         for (int e = tid; e < JP * JP; e += blockDim.x) {
           double sr = 0.0, si = 0.0;
           const cplx<T>* src = Gpart + (size_t)pi * nch * JP * JP + e;
@@ -1124,12 +1138,20 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
         __shared__ int s_need;
         if (tid == 0) s_need = 0;
         __syncthreads();
-        const bool full_e = (sweep == 0) || verify;
+        // the test: |G_ij| > max(tol sqrt(G_ii G_jj), floor); the floor is
+        // the larger of the global one (initial largest row) and floor_rel
+        // times the pair's largest row norm, the level to which a rotation
+        // derived from this pair's Gram resolves its entries (rows gain norm
+        // as the sweeps concentrate it, so the initial scale alone can sit
+        // below what the pair solve can reach and the sweeps never end)
+        double gpmax = 0.0;
+        for (int i = 0; i < JP; ++i) gpmax = fmax(gpmax, (double)Gs[i * LD + i].x);
+        const double pfloor = fmax((double)floor_abs, (double)floor_rel * gpmax);
         for (int e = tid; e < (full_e ? JP * JP : JB * JB); e += blockDim.x) {
           const int i = full_e ? e / JP : e / JB, j = full_e ? e % JP : JB + e % JB;
           if (i >= j) continue;
           const double aij = hypot(Gs[i * LD + j].x, Gs[i * LD + j].y);
-          const double thr = fmax((double)tol_rel * sqrt(fabs(Gs[i * LD + i].x * Gs[j * LD + j].x)), (double)floor_abs);
+          const double thr = fmax((double)tol_rel * sqrt(fabs(Gs[i * LD + i].x * Gs[j * LD + j].x)), pfloor);
           if (aij > thr) s_need = 1;
         }
         __syncthreads();
@@ -1140,17 +1162,29 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
           // cross entries (E skew-Hermitian), made unitary to rounding by
           // Newton-Schulz steps (J^H J = I - E^2 to start), leaves O(|E|^2)
           // off-diagonals -- quadratic like the Jacobi endgame but with O(1)
-          // sequential steps. Taken when every cross |E_ij| < 0.01 (so
-          // |J^H J - I| <= 512 * 1e-4 and the polish converges in a few
-          // steps) outside full-Gram sweeps; else the inner solve.
-          int first_order = 0;
+          // sequential steps. Those O(|E|^2) residues also land inside the
+          // blocks, which cross-only sweeps assume orthogonal, so the step is
+          // taken only where they stay below the convergence test: every
+          // cross |E_ij| < 0.01 (so |J^H J - I| <= 512 * 1e-4 and the polish
+          // converges in a few steps) and JB max|E|^2 max_k G_kk <=
+          // max(tol min_k G_kk, floor); outside full-Gram sweeps; else the
+          // inner solve.
+          int first_order = 0, exact = 1;
           if (!full_e) {
+            double gmin = 1e300, gmax = 0.0;
+            for (int i = 0; i < JP; ++i) {
+              const double d = (double)Gs[i * LD + i].x;
+              gmin = fmin(gmin, d);
+              gmax = fmax(gmax, d);
+            }
+            const double e2lim = gmax > 0.0 ? fmax((double)tol_rel * gmin, pfloor) / (JB * gmax) : 0.0;
             int ok = 1;
             for (int e = tid; e < JB * JB; e += blockDim.x) {
               const int i = e / JB, j = JB + e % JB;
               const double gap = fabs((double)Gs[j * LD + j].x - (double)Gs[i * LD + i].x);
-              const double g = hypot((double)Gs[i * LD + j].x, (double)Gs[i * LD + j].y);
-              if (!(g < 0.01 * gap)) ok = 0;
+              const double gx = (double)Gs[i * LD + j].x, gy = (double)Gs[i * LD + j].y;
+              const double g2 = gx * gx + gy * gy;
+              if (!(g2 < 1e-4 * gap * gap && g2 <= e2lim * gap * gap)) ok = 0;
             }
             first_order = __syncthreads_and(ok);
           }
@@ -1176,8 +1210,8 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
               s_gmax = gm;
             }
             __syncthreads();
-            bj_inner_eig<T>(Gs, Vs + JP * LD, Vs, 4.0 * (double)eps_of<T>::value * sqrt((double)JP),
-                            32.0 * (double)eps_of<T>::value * (double)s_gmax, 3);
+            exact = bj_inner_eig<T>(Gs, Vs + JP * LD, Vs, 4.0 * (double)eps_of<T>::value * sqrt((double)JP),
+                                    32.0 * (double)eps_of<T>::value * (double)s_gmax, 3);
             // FP32: remove the rounding drift of J (FP64 rotations keep it at 1e-16)
             if constexpr (sizeof(T) == 4) bj_polish_unitary<T>(Vs, Gs, Vs + JP * LD);
           }
@@ -1186,11 +1220,13 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
             act_flag[pi] = 1;
             last_mod[P] = gstamp;
             last_mod[Q] = gstamp;
+            wdirty[P] = wdirty[Q] = exact ? 0 : 1;
             atomicAdd(&ctl->active[sweep], 1);
           }
         } else if (tid == 0) {
           act_flag[pi] = 0;
           last_clean[(size_t)P * N + Q] = gstamp;
+          if (full_e) wdirty[P] = wdirty[Q] = 0;   // verified by the full Gram
         }
         __syncthreads();
       }

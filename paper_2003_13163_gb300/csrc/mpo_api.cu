@@ -34,6 +34,8 @@
 #include <algorithm>
 #include <type_traits>
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <thread>
 
 #include "../../include/mpo.h"
@@ -183,12 +185,30 @@ static int cap_of(int b, int n, int chi_max) {
 }
 
 // ------------------------------------------------------- eigen-solve launch --
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` on the
+// current device. The limit is a property of the function shared by every
+// host thread (the batching form launches from several), so it only ever
+// grows: a thread that needs less never lowers it under another's launch.
+static cudaError_t ensure_dynamic_smem(const void* fn, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> cur;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  int& c = cur[std::make_pair(fn, dev)];
+  if (bytes <= c) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) c = bytes;
+  return e;
+}
+
 template <typename T>
 static cudaError_t launch_jacobi(cudaStream_t st, cplx<T>* G, int m, cplx<T>* V, T* w, GridCtl* ctl,
                                  int max_sweeps, double timeout_s, int num_sms) {
   const int N = m + (m & 1);
   const size_t smem = sizeof(JRot<T>) * (size_t)std::max(1, N / 2);
-  cudaError_t e = cudaFuncSetAttribute(jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_dynamic_smem((const void*)jacobi_kernel<T>, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel<T>, 256, smem);
@@ -213,7 +233,7 @@ static cudaError_t launch_select(cudaStream_t st, const T* w, int m, int cap, do
   int P = 1;
   while (P < m) P <<= 1;
   const size_t smem = (size_t)P * (sizeof(double) + sizeof(int));
-  cudaError_t e = cudaFuncSetAttribute(select_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_dynamic_smem((const void*)select_kernel<T>, (int)smem);
   if (e != cudaSuccess) return e;
   select_kernel<T><<<1, 1024, smem, st>>>(w, m, cap, cutoff2, perm, lam2, info, disc, lognorm, S, sch);
   return cudaGetLastError();
@@ -253,7 +273,7 @@ static cudaError_t launch_block_jacobi(cudaStream_t st, cplx<T>* X, int r, int c
                                       cplx<T>* Gpart, size_t gpart_slots, cplx<T>* Jbuf, int* act, size_t act_ints,
                                       OSCtl* ctl, int max_sweeps, double timeout_s, int num_sms) {
   const int smem = block_jacobi_smem_bytes<T>();
-  cudaError_t e = cudaFuncSetAttribute(block_jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = ensure_dynamic_smem((const void*)block_jacobi_kernel<T>, smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, block_jacobi_kernel<T>, 256, smem);
@@ -266,11 +286,15 @@ static cudaError_t launch_block_jacobi(cudaStream_t st, cplx<T>* X, int r, int c
   const int blocks = std::max(1, std::min(per_sm * num_sms, items));
   e = cudaMemsetAsync(ctl, 0, sizeof(OSCtl), st);
   if (e != cudaSuccess) return e;
-  // relative criterion at the rounding level of a length-c dot product; the
-  // absolute floor sits above the rounding of the pair Gram itself, which the
-  // block rotation cannot resolve below
-  const T tol_rel = (T)(2.0 * eps_of<T>::value * std::sqrt((double)std::max(c, 1)));
-  const T floor_rel = (T)(16.0 * eps_of<T>::value * std::sqrt((double)std::max(c, 1)));
+  // relative criterion at the rounding level of a length-c dot product, but
+  // never below twice the stopping level of the in-CTA pair solve (4 eps
+  // sqrt(JP)) plus the rounding of applying a JP-term rotation: with short
+  // rows (c < 16 JP) a tighter outer test than the inner solve can meet
+  // makes the sweeps rotate the same pairs for ever; the absolute floor sits
+  // above the rounding of the pair Gram itself, which the block rotation
+  // cannot resolve below
+  const T tol_rel = (T)(2.0 * eps_of<T>::value * std::max(std::sqrt((double)std::max(c, 1)), 4.0 * std::sqrt((double)JP)));
+  const T floor_rel = (T)(16.0 * eps_of<T>::value * std::max(std::sqrt((double)std::max(c, 1)), 4.0));
   long long timeout_ns = (long long)(timeout_s * 1e9);
   void* args[] = {&X, &r, &c, &ldx, &Ut, &w, &Gpart, &Jbuf, &act, &ctl, &max_sweeps, (void*)&tol_rel,
                   (void*)&floor_rel, &timeout_ns};
@@ -326,11 +350,9 @@ template <typename T> static cplx<T>* S_(mpo_ctx* h, int k) { return (cplx<T>*)h
 static cudaError_t tc_cgemm(cudaStream_t st, int M, int N, int K, const float2* A, int lda, const float2* B, int ldb,
                             float2* C, int ldc, const double* alpha_dev, double alpha_host, int* status,
                             double timeout_s) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(tc_cgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tcg::SMEM_BYTES);
+  {
+    cudaError_t e = ensure_dynamic_smem((const void*)tc_cgemm_kernel, tcg::SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    attr_set = true;
   }
   dim3 grid((N + tcg::BNC - 1) / tcg::BNC, (M + tcg::BM - 1) / tcg::BM);
   tc_cgemm_kernel<<<grid, 128, tcg::SMEM_BYTES, st>>>(M, N, K, A, lda, B, ldb, C, ldc, alpha_dev, alpha_host, status,
@@ -1091,8 +1113,10 @@ static int static_scratch_address(StaticSvdScratch** out) {
   // one lookup per device, done with that device current (the symbol's host
   // name is only a stand-in; the device address comes from the runtime)
   static void* addr[64] = {nullptr};
+  static std::mutex mu;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return MPO_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(mu);
   if (!addr[dev]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_static_svd_scratch);

@@ -115,3 +115,14 @@ def test_batch_rejects_single_instance_calls(M):
     assert b._lib.mpo_entropy(b.h, S.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), None, None) == -1
     assert b"batch" in b._lib.mpo_last_error(b.h)
     b.close()
+
+
+def test_batch_many_mixed_instances_threads(M):
+    """Many instances of different sizes (so their kernels ask for different
+    launch resources) on eight worker threads give the one-thread results."""
+    circuits = [random_circuit(n, 4, 0.02, seed=50 + i) for i, n in enumerate([4, 6, 8, 10, 12, 14, 16] * 4)]
+    _, S1, tr1, _ = _run_batch(M, circuits, 32, "fp32", workers=1)
+    _, S8, tr8, _ = _run_batch(M, circuits, 32, "fp32", workers=8)
+    for i in range(len(circuits)):
+        assert np.array_equal(S1[i], S8[i]), f"instance {i}"
+        assert np.array_equal(tr1[i], tr8[i]), f"instance {i}"
