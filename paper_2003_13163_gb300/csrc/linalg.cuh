@@ -929,7 +929,8 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
   int* last_mod = act_flag + npairs;
   int* wdirty = last_mod + N;   // 1: the block's own rows were left by an inexact pair solve
   int* last_clean = wdirty + N;
-  for (size_t e = gtid; e < 2 * (size_t)N + (size_t)N * N; e += gthreads) last_mod[e] = 0;
+  // every block starts unverified: its first pair forms the full Gram
+  for (size_t e = gtid; e < 2 * (size_t)N + (size_t)N * N; e += gthreads) last_mod[e] = (e >= (size_t)N && e < 2 * (size_t)N) ? 1 : 0;
   for (long i = gwarp; i < r; i += nwarps) {
     T s = T(0);
     for (int j = lane; j < c; j += 32) { const cplx<T> x = ldcg(&X[(size_t)i * ldx + j]); s += x.x * x.x + x.y * x.y; }
@@ -949,16 +950,21 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
   bool converged = (r <= 1);
   bool verify = false;   // this sweep forms full Grams to confirm convergence
   for (; sweep < max_sweeps && !converged; ++sweep) {
-    for (int rd = 0; rd < N - 1; ++rd) {
+    // a verification pass is one round of full Grams (two when a block sits
+    // out round 0): every round pairs each block once, so it re-checks the
+    // rows inside every block; the cross blocks were just found orthogonal
+    const int nrounds = verify ? ((nb & 1) ? 2 : 1) : N - 1;
+    for (int rd = 0; rd < nrounds; ++rd) {
       unsigned long long tph = (blockIdx.x == 0 && tid == 0) ? global_timer_ns() : 0ull;
       // ---- phase G: partial Grams of each pair over column chunks ---------
-      // Sweep 0 forms the full 2JB x 2JB Gram. From sweep 1 on every block's
-      // own rows are mutually orthogonal (each round orthogonalises all rows
-      // of a pair, and a block's rows change only when it is paired), so only
-      // the JB x JB cross block X_P X_Q^H and the row norms are formed; the
-      // diagonal blocks are taken as diagonal. The chunk is staged GW columns
-      // at a time with every load in flight before the first store.
-      const bool full_gram = (sweep == 0) || verify;
+      // A pair with an unverified block (every block until its first pair
+      // solve, and after an inexact one) and every pair of a verification
+      // pass form the full 2JB x 2JB Gram. Otherwise each block's own rows
+      // are mutually orthogonal (a pair solve orthogonalises all its rows,
+      // and a block's rows change only when it is paired), so only the
+      // JB x JB cross block X_P X_Q^H and the row norms are formed; the
+      // diagonal blocks are taken as diagonal.
+      const bool full_gram = verify;
       const long nitems = (long)npairs * nch;
       // The CTA's work is the sequence of (item, sub-chunk) stages of its
       // items; a ring of BJ_NB tiles keeps BJ_NB stages in flight (cp.async,
@@ -1339,8 +1345,9 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
       if (!grid_barrier(&ctl->g, nblk, timeout_ns)) return;
       if (blockIdx.x == 0 && tid == 0) ctl->phase_ns[2] += global_timer_ns() - tph;
     }
-    // a quiet sweep ends the solve only if it formed full Grams (sweep 0 or a
-    // verification sweep); a quiet cross-only sweep triggers a verification
+    // a quiet sweep ends the solve only if it checked every block's own rows:
+    // sweep 0 (each block's first pair forms its full Gram) or a verification
+    // pass; a quiet cross-only sweep triggers a verification pass
     const bool quiet = atomicAdd(&ctl->active[sweep], 0) == 0;
     const bool was_full = (sweep == 0) || verify;
     if (quiet && was_full) converged = true;
