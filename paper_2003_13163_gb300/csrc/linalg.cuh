@@ -1024,18 +1024,15 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
         // full: thread (ti, tj) owns G[ti + 16a][tj + 16b];
         // cross: k-slice g = tid / 16 (k = g, g + 16, ...), member m = tid % 16
         // owns C[4 mi + i][4 mj + j], mi = m / 4, mj = m % 4, and the norms of
-        // rows 4 mi + i (mj == 0) and JB + 4 mj + j (mi == 0)
+        // rows 4 mi + mj and JB + 4 mj + mi (each row's norm on one member)
         const int ti = tid >> 4, tj = tid & 15;
         const int mi = (tid & 15) >> 2, mj = tid & 3;
         cplx<T> acc[4][4];
-        T nrmP[4], nrmQ[4];
+        T nrmP = T(0), nrmQ = T(0);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          nrmP[i] = T(0);
-          nrmQ[i] = T(0);
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
           for (int j = 0; j < 4; ++j) acc[i][j] = czero<T>();
-        }
         const int c0 = ch * JCW, c1 = min(c, c0 + JCW);
         const int nsub = (c1 - c0 + GW - 1) / GW;
         for (int s = 0; s < nsub; ++s, ++jseq) {
@@ -1059,13 +1056,13 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
                 av[i] = tile[(4 * mi + i) * TS + k];
                 bv[i] = tile[(JB + 4 * mj + i) * TS + k];
               }
+              const cplx<T> np_ = tile[(4 * mi + mj) * TS + k], nq_ = tile[(JB + 4 * mj + mi) * TS + k];
+              nrmP += np_.x * np_.x + np_.y * np_.y;
+              nrmQ += nq_.x * nq_.x + nq_.y * nq_.y;
 #pragma unroll
-              for (int i = 0; i < 4; ++i) {
-                nrmP[i] += av[i].x * av[i].x + av[i].y * av[i].y;
-                nrmQ[i] += bv[i].x * bv[i].x + bv[i].y * bv[i].y;
+              for (int i = 0; i < 4; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) cfma<T>(acc[i][j], av[i], cconj<T>(bv[j]));
-              }
             }
           }
           __syncthreads();                      // the tile is free: refill it
@@ -1082,15 +1079,14 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
           // reduce the 16 k-slices in a fixed order (deterministic, so the
           // same input always gives the same factorisation): half-warp pairs
           // by shuffle, then the 8 warps through shared memory
-          constexpr int NV = 40;                                 // 16 complex + 4 + 4 norms
+          constexpr int NV = 34;                                 // 16 complex + 2 norms
           T vals[NV];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
+          for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) { vals[2 * (4 * i + j)] = acc[i][j].x; vals[2 * (4 * i + j) + 1] = acc[i][j].y; }
-            vals[32 + i] = nrmP[i];
-            vals[36 + i] = nrmQ[i];
-          }
+          vals[32] = nrmP;
+          vals[33] = nrmQ;
 #pragma unroll
           for (int v = 0; v < NV; ++v) vals[v] += __shfl_xor_sync(0xffffffffu, vals[v], 16);
           if ((tid & 31) < 16) {
@@ -1110,8 +1106,11 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
               v = mk<T>(sr, upper ? si : -si);
             } else if (i == j) {
               T s = T(0);
-              if (i < JB) { const int m = (i >> 2) * 4; for (int w = 0; w < 8; ++w) s += red[(w * 16 + m) * NV + 32 + (i & 3)]; }
-              else { const int m = (i - JB) >> 2; for (int w = 0; w < 8; ++w) s += red[(w * 16 + m) * NV + 36 + ((i - JB) & 3)]; }
+              if (i < JB) { for (int w = 0; w < 8; ++w) s += red[(w * 16 + i) * NV + 32]; }        // member i
+              else {
+                const int q = i - JB, m = 4 * (q & 3) + (q >> 2);                                   // 4 mi + mj, mj = q / 4, mi = q % 4
+                for (int w = 0; w < 8; ++w) s += red[(w * 16 + m) * NV + 33];
+              }
               v = mk<T>(s, T(0));
             }
             stcg(&Gp[e], v);
@@ -1281,8 +1280,22 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
         for (int q = 0; q < BJ_NB; ++q) { issue(q); cp_async_commit(); }
         const int ty = tid >> 5, tx = tid & 31;
         int jseq = 0;
-        for (long item = blockIdx.x; item < aitems; item += nblk) {
-          if (!a_valid(item)) continue;
+        // J of the CTA's next item is loaded into registers while the current
+        // item computes, so its L2 round trip is off the critical path
+        constexpr int JPER = JP * JP / 256;
+        cplx<T> jpre[JPER];
+        auto load_j = [&](long it) {
+          const int pi_ = (int)(it / (nch + nchu));
+#pragma unroll
+          for (int u = 0; u < JPER; ++u) {
+            const int e = tid + 256 * u, i = e / JP, k = e % JP;
+            jpre[u] = ldcg(&Jbuf[(size_t)pi_ * JP * JP + k * JP + i]);
+          }
+        };
+        long item = blockIdx.x;
+        while (item < aitems && !a_valid(item)) item += nblk;
+        if (item < aitems) load_j(item);
+        for (; item < aitems;) {
           const int pi = (int)(item / (nch + nchu)), ch = (int)(item % (nch + nchu));
           int P = rr_player(pi, rd, N), Q = rr_player(N - 1 - pi, rd, N);
           if (P > Q) { int t_ = P; P = Q; Q = t_; }
@@ -1290,12 +1303,15 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
           cplx<T>* M = onU ? Ut : X;
           const int ld = onU ? r : ldx, ncol = onU ? r : c;
           const int c0 = (onU ? ch - nch : ch) * JCW, c1 = min(ncol, c0 + JCW);
-          for (int e = tid; e < JP * JP; e += blockDim.x) {
+#pragma unroll
+          for (int u = 0; u < JPER; ++u) {
             // Js[i][k] = (J^H)[i][k] = conj(J[k][i])  or  (J^T)[i][k] = J[k][i]
-            const int i = e / JP, k = e % JP;
-            const cplx<T> v = ldcg(&Jbuf[(size_t)pi * JP * JP + k * JP + i]);
-            Js[i * LD + k] = onU ? v : cconj<T>(v);
+            const int e = tid + 256 * u, i = e / JP, k = e % JP;
+            Js[i * LD + k] = onU ? jpre[u] : cconj<T>(jpre[u]);
           }
+          long next = item + nblk;
+          while (next < aitems && !a_valid(next)) next += nblk;
+          if (next < aitems) load_j(next);
           int orow[4];
 #pragma unroll
           for (int a_ = 0; a_ < 4; ++a_) {
@@ -1338,6 +1354,7 @@ __global__ void __launch_bounds__(256) block_jacobi_kernel(cplx<T>* X, int r, in
             issue(jseq % BJ_NB);
             cp_async_commit();
           }
+          item = next;
         }
         cp_async_wait<0>();
         __syncthreads();
