@@ -742,6 +742,10 @@ __device__ int bj_inner_eig(cplx<TI>* G0, cplx<TI>* G1, cplx<TI>* Vs /*JP x JP, 
         if (pl > ql) { const int t_ = pl; pl = ql; ql = t_; }
         bj_rot_params<TI>(Gc, pl, ql, tol2, flo2, cl, sl, url, uil);
       }
+      // every warp derives the same table from the same matrix, so a round
+      // with nothing to rotate is skipped by all threads alike (no writes,
+      // no barrier)
+      if (!__any_sync(0xffffffffu, sl != TI(0))) continue;
       const TI ca = __shfl_sync(0xffffffffu, cl, ia), sa = __shfl_sync(0xffffffffu, sl, ia);
       const TI ura = __shfl_sync(0xffffffffu, url, ia), uia = __shfl_sync(0xffffffffu, uil, ia);
       const TI cb = __shfl_sync(0xffffffffu, cl, ib), sb = __shfl_sync(0xffffffffu, sl, ib);
