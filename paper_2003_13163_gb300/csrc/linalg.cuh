@@ -744,7 +744,9 @@ __device__ int bj_inner_eig(cplx<TI>* G0, cplx<TI>* G1, cplx<TI>* Vs /*JP x JP, 
       }
       // every warp derives the same table from the same matrix, so a round
       // with nothing to rotate is skipped by all threads alike (no writes,
-      // no barrier)
+      // no barrier); the function therefore ends with a barrier, so that no
+      // thread reuses G0 / G1 (the caller's polish scratch) while another is
+      // still reading the last skipped rounds' table
       if (!__any_sync(0xffffffffu, sl != TI(0))) continue;
       const TI ca = __shfl_sync(0xffffffffu, cl, ia), sa = __shfl_sync(0xffffffffu, sl, ia);
       const TI ura = __shfl_sync(0xffffffffu, url, ia), uia = __shfl_sync(0xffffffffu, uil, ia);
@@ -784,8 +786,12 @@ __device__ int bj_inner_eig(cplx<TI>* G0, cplx<TI>* G1, cplx<TI>* Vs /*JP x JP, 
       any |= __syncthreads_or(sb != TI(0));
       cplx<TI>* t_ = Gc; Gc = Gn; Gn = t_;
     }
-    if (!any) return 1;
+    if (!any) {
+      __syncthreads();   // rounds skipped without a barrier: no thread may leave while others still read Gc
+      return 1;
+    }
   }
+  __syncthreads();
   return 0;
 }
 
