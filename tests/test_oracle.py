@@ -257,3 +257,21 @@ def test_peak_depth_and_height_fig5(key):
     assert int(np.argmax(smax)) + 1 == g["D_star"]
     assert abs(smax.max() - g["S_star"]) < 0.2
     assert min(tr) >= g["trace_min"]
+
+
+def test_ensemble_instances_recipe():
+    """The batching workload's inputs: (n_i, p_i) from the stated choices,
+    depth 2 n_i, brickwork gate counts per step, reproducible per seed, and
+    instance i's gates equal to a single circuit drawn with seed 1000 + i."""
+    from paper_2003_13163_gb300.circuits import ensemble_instances, n_gates
+    a = ensemble_instances(12, seed=4)
+    b = ensemble_instances(12, seed=4)
+    assert [c.n for c in a] == [c.n for c in b]
+    for i, c in enumerate(a):
+        assert c.n in (16, 24, 32, 40, 48, 56, 64)
+        assert float(c.p[0][0]) in (0.005, 0.01, 0.02, 0.05)
+        assert c.depth == 2 * c.n
+        assert [len(g) for g in c.gates[:2]] == [n_gates(c.n, 0), n_gates(c.n, 1)]
+        ref = random_circuit(c.n, c.depth, float(c.p[0][0]), 1000 + i)
+        assert np.array_equal(ref.gates[0], c.gates[0]) and np.array_equal(ref.gates[-1], c.gates[-1])
+    assert len({c.n for c in ensemble_instances(64, seed=4)}) > 3      # the sizes are mixed
