@@ -280,11 +280,13 @@ int mpo_svd_last_stats(int *sweeps, double *phase_ms3);
  *
  * Same contract and result as mpo_svd(r, c, X, w, Ut, prec, max_sweeps, 1,
  * stream) for r <= 512 and c <= 2048, but every piece of scratch the solver
- * needs lives in one device array built into the library (about 3 MB per
+ * needs lives in one device array built into the library (about 1.7 MB per
  * GPU that uses it, held until the process exits). It is meant for callers
- * that must not call cudaMalloc when they need the factorisation, e.g. code
- * that runs between cudaStreamBeginCapture and cudaStreamEndCapture, or a host
- * that grants the library a fixed memory budget ahead of time.
+ * that must not call cudaMalloc when they need the factorisation: code that
+ * runs inside a memory allocator's own hooks (a framework's custom-allocator
+ * callback, where allocating again would re-enter the allocator), or a host
+ * that grants the library a fixed memory budget ahead of time and accounts
+ * for every byte it hands out.
  *
  *   - Larger matrices are rejected with MPO_ERR_ARG; mpo_last_error(NULL) says
  *     which limit was hit. Other errors as for mpo_svd.

@@ -1084,9 +1084,9 @@ int mpo_svd(int r, int c, void* X, void* w, void* Ut, mpo_precision prec, int ma
 // Block-Jacobi SVD with built-in scratch (mpo_svd_static).
 //
 // Some callers cannot allocate device memory at the point where they need an
-// SVD: code running while a CUDA graph is being captured (where cudaMalloc
-// would break the capture), allocators' own callbacks, or hosts that hand out
-// a fixed memory budget up front. For them this entry point keeps the block
+// SVD: code running inside an allocator's own callbacks (allocating again
+// would re-enter the allocator), or hosts that hand out a fixed memory budget
+// up front and account for every byte. For them this entry point keeps the block
 // Jacobi's scratch (barrier/status block, pair Gram partials, rotations) in
 // one file-scope device array that exists for as long as the library is
 // loaded on each GPU that uses it. The caller only passes the matrix and the

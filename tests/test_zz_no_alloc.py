@@ -1,8 +1,9 @@
 """The SVD entry point that allocates nothing (mpo_svd_static).
 
 Some callers cannot call cudaMalloc when they need a factorisation, for
-example code running inside a CUDA-graph capture or under a fixed memory
-budget. mpo_svd_static keeps its scratch in a device array built into the
+example code running inside an allocator's own callbacks (allocating again
+would re-enter the allocator) or under a fixed memory budget granted up
+front. mpo_svd_static keeps its scratch in a device array built into the
 library. Here it is called through the C ABI and compared with the allocating
 entry point (mpo_svd, block form) on the same inputs, twice in a row, since
 every call reuses the same scratch. This file is collected last on purpose.
