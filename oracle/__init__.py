@@ -17,6 +17,11 @@ Modules (each function cites the passage it follows):
   mpo       - Oracle M: the MPO in mixed canonical form updated gate by gate
               with QR/SVD centre moves and local truncation (Note added), plus
               the end-of-step Schmidt sweep giving lambda at every bond.
+  vidal     - Oracle V: App. A's canonical (Gamma, lambda) update taken
+              literally, with its global left and right re-factorisation after
+              every gate and the divisions by lambda; a third route to the
+              same truncated dynamics, for untruncated or mildly truncated
+              cases.
   entropy   - MPO entanglement entropy (Sec. 3.3) and Page's mean entropy.
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against

@@ -275,3 +275,49 @@ def test_ensemble_instances_recipe():
         ref = random_circuit(c.n, c.depth, float(c.p[0][0]), 1000 + i)
         assert np.array_equal(ref.gates[0], c.gates[0]) and np.array_equal(ref.gates[-1], c.gates[-1])
     assert len({c.n for c in ensemble_instances(64, seed=4)}) > 3      # the sizes are mixed
+
+
+# ------------------------------------------------ Oracle V (App. A, literal) --
+@pytest.mark.parametrize("n,chi,p,seed,depth", [(6, 64, 0.02, 31, 8), (8, 256, 0.05, 32, 8)])
+def test_vidal_update_matches_dense_exact(n, chi, p, seed, depth):
+    """App. A's global (Gamma, lambda) update and the dense route agree when
+    nothing is truncated: every S_l after every step and the final |rho>>."""
+    from oracle import vidal
+    c = random_circuit(n, depth, p, seed=seed)
+    v = vidal.run(c, chi)
+    d = dense.run(c, chi)
+    assert np.abs(v.S - d.S).max() < 1e-10
+    assert np.abs(v.final.to_dense() - d.final).max() < 1e-12
+
+
+@pytest.mark.parametrize("n,chi,p,seed,depth", [(8, 16, 0.05, 2, 6), (8, 4, 0.02, 5, 6), (10, 16, 0.05, 3, 4)])
+def test_vidal_update_matches_dense_truncated(n, chi, p, seed, depth):
+    """With truncation: App. A keeps the chi largest values at the gate's bond
+    and only re-canonicalises elsewhere, so it reproduces the dense
+    truncation, the discarded weights included (the equivalence of App. A and
+    the local update of the Note added)."""
+    from oracle import vidal
+    c = random_circuit(n, depth, p, seed=seed)
+    v = vidal.run(c, chi, 1e-10)
+    d = dense.run(c, chi, 1e-10)
+    assert sum(w.sum() for w in d.discarded) > 0.0
+    assert np.abs(v.S - d.S).max() < 1e-9
+    np.testing.assert_allclose(np.concatenate(v.discarded), np.concatenate(d.discarded), atol=1e-12)
+    assert np.abs(v.final.to_dense() - d.final).max() < 1e-11
+
+
+def test_vidal_lambdas_are_the_schmidt_values():
+    """After every gate the lambda vectors App. A maintains are the exact
+    operator-Schmidt values of |rho>> at every cut (the canonical form)."""
+    from oracle import vidal
+    c = random_circuit(8, 5, 0.03, seed=9)
+    m = vidal.VidalMPO(8)
+    for t in range(1, c.depth + 1):
+        for U, p, l in zip(c.gates[t - 1], c.p[t - 1], layer_bonds(8, c.parity(t))):
+            m.apply(l, channels.noisy_gate_superop(U, p), 256, 1e-12)
+            T = m.to_dense()
+            for b in range(1, 8):
+                ref = dense.schmidt_values(T, b)
+                k = len(m.lam[b])
+                np.testing.assert_allclose(m.lam[b], ref[:k], atol=1e-11 * ref[0])
+                assert ref[k:].sum() < 1e-9 * ref[0] if k < len(ref) else True
