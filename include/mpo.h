@@ -45,11 +45,22 @@ extern "C" {
 typedef struct mpo_ctx *mpo_handle;
 
 /* Arithmetic of the path.
- *   MPO_FP64: complex128 site tensors, every contraction and eigen-solve in FP64
- *             (the plain form).
- *   MPO_FP32: complex64 site tensors and FP32 contractions and eigen-solves;
- *             Schmidt-value normalisation, entropy and log-norm stay FP64. */
-typedef enum { MPO_FP64 = 0, MPO_FP32 = 1 } mpo_precision;
+ *   MPO_FP64:       complex128 site tensors, every contraction and eigen-solve in
+ *                   FP64 (the plain form).
+ *   MPO_FP32:       complex64 site tensors and FP32 contractions and eigen-solves;
+ *                   Schmidt-value normalisation, entropy and log-norm stay FP64.
+ *                   Fast, but its entropies differ from the FP64 form by ~1e-3.
+ *   MPO_MIXED_FP32: the precision form. complex128 site tensors; every truncated
+ *                   SVD (App. A) and centre move starts from the FP32 one-sided
+ *                   Jacobi SVD of an FP32 copy, whose m = chi_max + oversample
+ *                   leading left singular vectors are refined in FP64 by
+ *                   refine_steps Rayleigh-Ritz-accelerated subspace-iteration
+ *                   steps and a final Rayleigh-Ritz projection with an FP64
+ *                   Hermitian eigen-solve of the m x m projected Gram; the
+ *                   singular values, their normalisation and the entropy are
+ *                   FP64. Matches the FP64 form to |dS| <= 1e-6 and a kept-theta
+ *                   relative Frobenius error <= 1e-7 per gate. */
+typedef enum { MPO_FP64 = 0, MPO_FP32 = 1, MPO_MIXED_FP32 = 2 } mpo_precision;
 
 /* Which bonds mpo_entropy reports.
  *   MPO_S_ALL_BONDS: the end-of-step Schmidt sweep computes lambda at every bond.
@@ -71,7 +82,9 @@ typedef struct {
   int eig_max_sweeps;       /* cap on Jacobi sweeps per SVD [40, at most 64]; reaching it -> MPO_ERR_NOCONV */
   double sv_rel_cutoff;     /* drop Schmidt values lambda <= cutoff * lambda_max at every
                                factorisation [1e-12 for FP64, 1e-6 for FP32: the rounding
-                               floor of the one-sided Jacobi SVD]; <= 0 selects the default */
+                               floor of the one-sided Jacobi SVD; 1e-7 for MPO_MIXED_FP32:
+                               the floor of its FP64 Gram eigen-solve]; <= 0 selects the
+                               default */
   size_t arena_cap_bytes;   /* refuse device allocations above this total [0 = no cap] */
   mpo_entropy_mode smode;   /* [MPO_S_ALL_BONDS] */
   double barrier_timeout_s; /* limit of each device-side grid-barrier wait [5.0] */
@@ -84,6 +97,11 @@ typedef struct {
   int tensor_cores;         /* FP32 only: > 0 runs the plain complex products (theta, centre
                                moves) on the tcgen05 tensor cores with 3 x TF32 split products
                                [0 = off: the SIMT FP32 kernel, currently the faster one] */
+  int oversample;           /* MPO_MIXED_FP32: extra FP32 singular vectors carried into the FP64
+                               refinement of a truncating SVD, beyond chi_max [0 = chi_max / 2;
+                               < 0 = none] */
+  int refine_steps;         /* MPO_MIXED_FP32: subspace-iteration steps before the final
+                               Rayleigh-Ritz projection of a truncating SVD [0 = 3; < 0 = none] */
 } mpo_opts;
 
 /* Fill *o with the defaults. */
@@ -94,7 +112,7 @@ void mpo_default_opts(mpo_opts *o);
  *   out        : receives the handle (set to NULL on failure).
  *   n_qubits   : even, 2 <= n_qubits <= 4096 (Sec. 2.1 takes n even).
  *   chi_max    : bond-dimension cap of the truncation (App. A), 1 <= chi_max <= 4096.
- *   prec       : MPO_FP64 or MPO_FP32.
+ *   prec       : MPO_FP64, MPO_FP32 or MPO_MIXED_FP32.
  *   cuda_stream: a cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream),
  *                or NULL for the legacy default stream.
  *   opts       : NULL for defaults.
@@ -268,6 +286,28 @@ int mpo_eigh(int m, void *A, void *w, void *V, mpo_precision prec, int max_sweep
  * (<= 64) is reached. */
 int mpo_svd(int r, int c, void *X, void *w, void *Ut, mpo_precision prec, int max_sweeps, int block,
             void *cuda_stream);
+
+/* The truncated SVD of every gate (App. A: keep the cap largest singular
+ * values, and only those above sv_rel_cutoff * the largest) in the arithmetic
+ * of precision prec, exported for tests: for MPO_MIXED_FP32 it is the FP32
+ * Jacobi SVD plus FP64 subspace refinement and Rayleigh-Ritz projection that
+ * the precision form applies to every theta'.
+ *   A     : device, r x c complex (complex128 for MPO_FP64 / MPO_MIXED_FP32,
+ *           complex64 for MPO_FP32), row-major, 1 <= r <= c, r <= 8192; not
+ *           modified.
+ *   cap   : the bond-dimension cap chi_max.
+ *   opts  : NULL for the defaults (sv_rel_cutoff, oversample, refine_steps,
+ *           eig_max_sweeps, block_jacobi_min_rows as in mpo_opts).
+ *   U     : device, r x cap complex (leading dimension cap): columns 0..k-1
+ *           receive the left singular vectors in descending order.
+ *   X     : device, cap x c complex: rows 0..k-1 receive lambda_j w_j^H, so
+ *           that U[:, :k] X[:k] is the kept part of A.
+ *   lam2  : host [cap]: the k kept squared singular values, descending.
+ *   k     : host: the kept count.
+ * Allocates its workspace per call and waits for the stream. Errors as
+ * mpo_svd; the message is in mpo_last_error(NULL). */
+int mpo_svd_truncated(int r, int c, const void *A, int cap, mpo_precision prec, const mpo_opts *opts, void *U,
+                      void *X, double *lam2, int *k, void *cuda_stream);
 
 /* Statistics of the last mpo_svd call made on the calling thread: the sweeps
  * it ran and, for the block variant, the wall time (ms) of its three phases

@@ -10,7 +10,8 @@
 //   op == 0: plain; op == 1: conjugate transpose.
 //   op(A)(i,k) = A[i*lda + k]      or conj(A[k*lda + i])
 //   op(B)(k,j) = B[k*ldb + j]      or conj(B[j*ldb + k])
-// alpha = alpha_host * (alpha_dev ? *alpha_dev : 1).
+// alpha = alpha_host * (alpha_dev ? *alpha_dev : 1); accumulate != 0 adds the
+// product to C instead of overwriting it (C and A / B must not overlap then).
 // CTA tile BM x BN, K-slab BK, 256 threads, each thread TM x TN outputs spaced
 // by 16 rows / 16 columns so that shared-memory reads broadcast along rows.
 // ---------------------------------------------------------------------------
@@ -18,7 +19,7 @@ template <typename T, int BM, int BN, int BK>
 __global__ void __launch_bounds__(256) cgemm_kernel(int M, int N, int K,
     const cplx<T>* __restrict__ A, int lda, int opA,
     const cplx<T>* __restrict__ B, int ldb, int opB,
-    cplx<T>* __restrict__ C, int ldc, const double* __restrict__ alpha_dev, double alpha_host) {
+    cplx<T>* __restrict__ C, int ldc, const double* __restrict__ alpha_dev, double alpha_host, int accumulate) {
   constexpr int TM = BM / 16, TN = BN / 16;
   __shared__ cplx<T> As[BK][BM];
   __shared__ cplx<T> Bs[BK][BN];
@@ -80,7 +81,11 @@ __global__ void __launch_bounds__(256) cgemm_kernel(int M, int N, int K,
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
       const int c = col0 + tx + 16 * j;
-      if (c < N) C[(size_t)r * ldc + c] = cscale<T>(acc[i][j], alpha);
+      if (c < N) {
+        cplx<T> v = cscale<T>(acc[i][j], alpha);
+        if (accumulate) v = cadd<T>(v, C[(size_t)r * ldc + c]);
+        C[(size_t)r * ldc + c] = v;
+      }
     }
   }
 }
@@ -88,10 +93,11 @@ __global__ void __launch_bounds__(256) cgemm_kernel(int M, int N, int K,
 template <typename T>
 inline cudaError_t cgemm(cudaStream_t st, int M, int N, int K, const cplx<T>* A, int lda, int opA,
                          const cplx<T>* B, int ldb, int opB, cplx<T>* C, int ldc,
-                         const double* alpha_dev = nullptr, double alpha_host = 1.0) {
+                         const double* alpha_dev = nullptr, double alpha_host = 1.0, int accumulate = 0) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   constexpr int BM = 64, BN = 64, BK = 8;
   dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+  if (K <= 0 && accumulate) return cudaSuccess;
   if (K <= 0) {  // empty contraction: C = 0
     for (int r = 0; r < M; ++r) {
       cudaError_t e = cudaMemsetAsync(C + (size_t)r * ldc, 0, sizeof(cplx<T>) * N, st);
@@ -99,7 +105,8 @@ inline cudaError_t cgemm(cudaStream_t st, int M, int N, int K, const cplx<T>* A,
     }
     return cudaSuccess;
   }
-  cgemm_kernel<T, BM, BN, BK><<<grid, 256, 0, st>>>(M, N, K, A, lda, opA, B, ldb, opB, C, ldc, alpha_dev, alpha_host);
+  cgemm_kernel<T, BM, BN, BK><<<grid, 256, 0, st>>>(M, N, K, A, lda, opA, B, ldb, opB, C, ldc, alpha_dev, alpha_host,
+                                                     accumulate);
   return cudaGetLastError();
 }
 
@@ -255,7 +262,9 @@ __global__ void __launch_bounds__(256) jacobi_kernel(cplx<T>* G, int m, cplx<T>*
 //   - bitonic sort of (value desc, index asc) in shared memory (stable order
 //     for exact ties), negative rounding values clamped to 0;
 //   - k = min(cap, #{lambda^2 > cutoff^2 * lambda_max^2}), at least 1;
-//   - sums in FP64: total = sum lambda^2, kept = sum of the k largest;
+//   - sums in FP64: total = sum lambda^2 (or *total_in, the squared Frobenius
+//     norm of the factorised matrix, when w holds Ritz values of a subspace
+//     only), kept = sum of the k largest;
 //   - outputs perm[0..k), lam2[0..k) (descending), info->k, info->kept,
 //     info->total; adds (total-kept)/total to *disc_acc and 0.5 log(kept) to
 //     *lognorm when those are non-null;
@@ -276,7 +285,8 @@ template <typename T>
 __global__ void __launch_bounds__(1024) select_kernel(const T* __restrict__ w, int m, int cap, double cutoff2,
                                                        int* __restrict__ perm, double* __restrict__ lam2,
                                                        SelectInfo* info, double* disc_acc, double* lognorm,
-                                                       double* S_out, double* schmidt_out) {
+                                                       double* S_out, double* schmidt_out,
+                                                       const double* __restrict__ total_in) {
   extern __shared__ unsigned char ssm[];
   int P = 1;
   while (P < m) P <<= 1;
@@ -317,7 +327,7 @@ __global__ void __launch_bounds__(1024) select_kernel(const T* __restrict__ w, i
   if (tid == 0) {
     double s = 0.0;
     for (int i = 0; i < (nt + 31) / 32; ++i) s += red[i];
-    s_tot = s;
+    s_tot = total_in ? *total_in : s;   // the factorised matrix's squared norm when w covers a subspace only
     s_max = key[0];
     const double thr = cutoff2 * key[0];
     int k = 0;

@@ -42,6 +42,7 @@
 #include "common.cuh"
 #include "linalg.cuh"
 #include "mpo_kernels.cuh"
+#include "mixed.cuh"
 #include "tcgemm.cuh"
 
 namespace {
@@ -55,6 +56,8 @@ struct HostSync {   // pinned read-back of the last select + eigen-solve
   GridCtl ctl;
   unsigned long long phase_ns[4];
   int tc_err;
+  GridCtl eig[8];     // FP64 eigen-solves of the last mixed factorisation
+  int chol_status;    // Cholesky QR pivot status of the last mixed factorisation
 };
 
 }  // namespace
@@ -106,6 +109,24 @@ struct mpo_ctx {
   int last_sweeps = 0;
   // kernel-class timing (mpo_profile): CUDA events recorded on h->st around
   // each launch, resolved lazily
+  // precision form (MPO_MIXED_FP32): complex128 sites, FP32 approximate SVD,
+  // FP64 refinement; buffers of the refinement (see msvd_select)
+  bool mixed = false;
+  bool vecs_conj = false;          // vecs holds rows conj(column of U) (mixed) instead of U^T
+  int mx_over = 0, mx_steps = 0;   // oversampling and refinement steps
+  int mx_mcap = 0;                 // largest m = min(r, chi_max + oversample)
+  float2 *mx_a32 = nullptr, *mx_ut32 = nullptr;
+  float* mx_w32 = nullptr;
+  int* mx_perm32 = nullptr;
+  double* mx_lam32 = nullptr;
+  SelectInfo* mx_info32 = nullptr;
+  double2 *mx_Q = nullptr, *mx_Q2 = nullptr, *mx_B = nullptr, *mx_T = nullptr;
+  double2 *mx_H = nullptr, *mx_V = nullptr, *mx_G = nullptr;
+  double* mx_w = nullptr;
+  GridCtl* mx_ctl = nullptr;       // one control block per FP64 eigen-solve of a factorisation
+  double2 *mx_linv = nullptr, *mx_ptmp = nullptr;   // Cholesky: diagonal-block inverses, panel scratch
+  int* mx_chst = nullptr;          // set when a Cholesky pivot was not positive
+  struct MxSync { GridCtl g32; GridCtl eig[8]; };
   bool prof = false;
   struct Pending { int cls; cudaEvent_t a, b; double flops, bytes; };
   std::vector<Pending> pend;
@@ -116,9 +137,10 @@ struct mpo_ctx {
   double prof_phase_ns[3] = {0, 0, 0};
 };
 
-enum { PK_SVD = 0, PK_SVD_SWEEP, PK_GEMM, PK_SUPEROP, PK_SELECT, PK_GATHER, PK_TRANSPOSE, PK_TRACE, PK_TCGEMM, PK_NCLASS };
+enum { PK_SVD = 0, PK_SVD_SWEEP, PK_GEMM, PK_SUPEROP, PK_SELECT, PK_GATHER, PK_TRANSPOSE, PK_TRACE, PK_TCGEMM,
+       PK_REFINE, PK_EIG64, PK_CONVERT, PK_NCLASS };
 static const char* kProfNames[PK_NCLASS] = {"svd_gate", "svd_sweep", "cgemm", "superop", "select", "gather", "transpose", "trace",
-                                            "tc_cgemm"};
+                                            "tc_cgemm", "refine_gemm", "eig_fp64", "convert"};
 
 static cudaEvent_t prof_event(mpo_ctx* h) {
   if (!h->evpool.empty()) { cudaEvent_t e = h->evpool.back(); h->evpool.pop_back(); return e; }
@@ -176,6 +198,9 @@ static int fail(mpo_ctx* h, int code, const std::string& m) {
       return fail((h), MPO_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e__)); \
   } while (0)
 
+// complex128 site tensors: the FP64 form and the precision form
+static bool dsite(const mpo_ctx* h) { return h->prec != MPO_FP32; }
+
 static int cap_of(int b, int n, int chi_max) {
   // min(chi_max, 4^b, 4^(n-b)) without overflow
   int e = std::min(b, n - b);
@@ -229,13 +254,13 @@ static cudaError_t launch_jacobi(cudaStream_t st, cplx<T>* G, int m, cplx<T>* V,
 template <typename T>
 static cudaError_t launch_select(cudaStream_t st, const T* w, int m, int cap, double cutoff2, int* perm,
                                  double* lam2, SelectInfo* info, double* disc, double* lognorm, double* S,
-                                 double* sch) {
+                                 double* sch, const double* total_in = nullptr) {
   int P = 1;
   while (P < m) P <<= 1;
   const size_t smem = (size_t)P * (sizeof(double) + sizeof(int));
   cudaError_t e = ensure_dynamic_smem((const void*)select_kernel<T>, (int)smem);
   if (e != cudaSuccess) return e;
-  select_kernel<T><<<1, 1024, smem, st>>>(w, m, cap, cutoff2, perm, lam2, info, disc, lognorm, S, sch);
+  select_kernel<T><<<1, 1024, smem, st>>>(w, m, cap, cutoff2, perm, lam2, info, disc, lognorm, S, sch, total_in);
   return cudaGetLastError();
 }
 
@@ -301,11 +326,213 @@ static cudaError_t launch_block_jacobi(cudaStream_t st, cplx<T>* X, int r, int c
   return cudaLaunchCooperativeKernel((const void*)block_jacobi_kernel<T>, dim3(blocks), dim3(256), args, smem, st);
 }
 
+// ---------------------------------------------------------------------------
+// Precision form: truncated SVD of a complex128 matrix X (r x c, r <= c,
+// leading dimension ldx) keeping at most cap singular values (App. A), with
+// the heavy lifting in FP32 and the accuracy won back in FP64.
+//   1. FP32 one-sided Jacobi SVD of fl32(X) -> approximate U (r x r), w.
+//   2. Q (r x m, FP64) = the m = min(r, cap + oversample) leading columns of U,
+//      made orthonormal to FP64 rounding by Newton-Schulz steps.
+//   3. If m < r (the truncation can bite), refine_steps subspace-iteration
+//      steps Q <- orth(X X^H Q) in FP64, each damping the components of the
+//      leading singular vectors outside span(Q) by (sigma_{m+1} / sigma_j)^2;
+//      orth is shifted Cholesky QR followed by two Cholesky QR passes
+//      (shifted CholeskyQR3, stable for condition numbers up to 1/eps).
+//      With m = r the span of Q is the whole row space already.
+//   4. Rayleigh-Ritz: B = Q^H X, H = B B^H = V diag(w) V^H (FP64 Jacobi
+//      eigen-solve). The Ritz values w are the squared singular values, Q V
+//      the left singular vectors and V^H B = Lambda W^H the scaled right ones.
+// Outputs follow the one-sided Jacobi convention of svd_select: rows 0..m-1
+// of X are overwritten with V^H B, h->vecs holds V^H Q^H (m x r, row j =
+// conj of left singular vector j: h->vecs_conj), h->mx_w the w; the select
+// kernel then sorts and truncates.
+// ---------------------------------------------------------------------------
+static cudaError_t mx_gemm(mpo_ctx* h, int M, int N, int K, const double2* A, int lda, int opA, const double2* B,
+                           int ldb, int opB, double2* C, int ldc, double alpha = 1.0, int accumulate = 0) {
+  ProfScope ps(h, PK_REFINE, 8.0 * M * N * K, (double)((size_t)M * K + (size_t)K * N + (size_t)M * N) * sizeof(double2));
+  return cgemm<double>(h->st, M, N, K, A, lda, opA, B, ldb, opB, C, ldc, nullptr, alpha, accumulate);
+}
+
+// Q (r x m) <- Q (3 I - Q^H Q) / 2, twice: from a basis orthonormal to ~1e-5
+// the defect falls to ~1e-10 and then to FP64 rounding.
+static int mx_orthonormalise(mpo_ctx* h, int r, int m) {
+  for (int it = 0; it < 2; ++it) {
+    CK(h, mx_gemm(h, m, m, r, h->mx_Q, m, 1, h->mx_Q, m, 0, h->mx_G, m));
+    {
+      ProfScope ps(h, PK_REFINE, 0.0, 2.0 * m * m * sizeof(double2));
+      ns_multiplier_kernel<<<grid_for((size_t)m * m, h->num_sms), 256, 0, h->st>>>(h->mx_G, m);
+      CK(h, cudaGetLastError());
+    }
+    CK(h, mx_gemm(h, r, m, m, h->mx_Q, m, 0, h->mx_G, m, 0, h->mx_Q2, m));
+    std::swap(h->mx_Q, h->mx_Q2);
+  }
+  return MPO_OK;
+}
+
+// G (m x m, leading dimension m) = L L^H in place (lower triangle), blocked
+// right-looking: per CHOL_NB panel the diagonal block is factored (and its
+// factor inverted) by chol_diag_kernel, the panel below becomes
+// G21 L11^{-H} and the trailing block is updated by G22 -= P P^H.
+static int mx_cholesky(mpo_ctx* h, double2* G, int m) {
+  CK(h, ensure_dynamic_smem((const void*)chol_diag_kernel, CHOL_SMEM));
+  for (int k0 = 0; k0 < m; k0 += CHOL_NB) {
+    const int b = std::min(CHOL_NB, m - k0);
+    double2* Li = h->mx_linv + (size_t)(k0 / CHOL_NB) * CHOL_NB * CHOL_NB;
+    {
+      ProfScope ps(h, PK_REFINE, 8.0 * b * b * b / 3.0, 2.0 * b * b * sizeof(double2));
+      chol_diag_kernel<<<1, 256, CHOL_SMEM, h->st>>>(G, m, k0, b, Li, h->mx_chst);
+      CK(h, cudaGetLastError());
+    }
+    const int rest = m - k0 - b;
+    if (rest > 0) {
+      CK(h, mx_gemm(h, rest, b, b, G + (size_t)(k0 + b) * m + k0, m, 0, Li, CHOL_NB, 1, h->mx_ptmp, CHOL_NB));
+      CK(h, cudaMemcpy2DAsync(G + (size_t)(k0 + b) * m + k0, (size_t)m * sizeof(double2), h->mx_ptmp,
+                              CHOL_NB * sizeof(double2), (size_t)b * sizeof(double2), rest, cudaMemcpyDeviceToDevice,
+                              h->st));
+      CK(h, mx_gemm(h, rest, rest, b, h->mx_ptmp, CHOL_NB, 0, h->mx_ptmp, CHOL_NB, 1, G + (size_t)(k0 + b) * (m + 1), m,
+                    -1.0, 1));
+    }
+  }
+  return MPO_OK;
+}
+
+// Y (r x m, leading dimension m) <- Y L^{-H} in place, L the Cholesky factor
+// in G: column block J becomes (Y_J - Y_{<J} L_{J,<J}^H) L_JJ^{-H}.
+static int mx_trsm(mpo_ctx* h, double2* Y, int r, int m, const double2* G) {
+  for (int j0 = 0; j0 < m; j0 += CHOL_NB) {
+    const int b = std::min(CHOL_NB, m - j0);
+    if (j0 > 0) CK(h, mx_gemm(h, r, b, j0, Y, m, 0, G + (size_t)j0 * m, m, 1, Y + j0, m, -1.0, 1));
+    CK(h, mx_gemm(h, r, b, b, Y + j0, m, 0, h->mx_linv + (size_t)(j0 / CHOL_NB) * CHOL_NB * CHOL_NB, CHOL_NB, 1,
+                  h->mx_ptmp, CHOL_NB));
+    CK(h, cudaMemcpy2DAsync(Y + j0, (size_t)m * sizeof(double2), h->mx_ptmp, CHOL_NB * sizeof(double2),
+                            (size_t)b * sizeof(double2), r, cudaMemcpyDeviceToDevice, h->st));
+  }
+  return MPO_OK;
+}
+
+// Y (r x m) <- an orthonormal basis of its span by Cholesky QR: G = Y^H Y
+// (+ shift_rel * trace(G) on the diagonal), G = L L^H, Y <- Y L^{-H}.
+static int mx_cholqr(mpo_ctx* h, double2* Y, int r, int m, double shift_rel) {
+  CK(h, mx_gemm(h, m, m, r, Y, m, 1, Y, m, 0, h->mx_G, m));
+  if (shift_rel > 0.0) {
+    add_trace_shift_kernel<<<1, 1024, 0, h->st>>>(h->mx_G, m, shift_rel);
+    CK(h, cudaGetLastError());
+  }
+  int rc = mx_cholesky(h, h->mx_G, m);
+  if (rc) return rc;
+  return mx_trsm(h, Y, r, m, h->mx_G);
+}
+
+// Shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto & Yanagisawa,
+// SIAM J. Sci. Comput. 2020): one Cholesky QR with the shift
+// 11 (r m + m (m + 1)) u ||Y||^2 makes the basis well conditioned, two plain
+// passes make it orthonormal to rounding.
+static int mx_scholqr3(mpo_ctx* h, double2* Y, int r, int m) {
+  const double u = 1.1102230246251565e-16;
+  int rc = mx_cholqr(h, Y, r, m, 11.0 * ((double)r * m + (double)m * (m + 1)) * u);
+  if (!rc) rc = mx_cholqr(h, Y, r, m, 0.0);
+  if (!rc) rc = mx_cholqr(h, Y, r, m, 0.0);
+  return rc;
+}
+
+// B = Q^H X (m x c), H = B B^H, FP64 eigen-solve H = V diag(w) V^H using
+// control block slot `slot`.
+static int mx_ritz(mpo_ctx* h, const double2* X, int r, int c, int ldx, int m, int slot) {
+  CK(h, mx_gemm(h, m, c, r, h->mx_Q, m, 1, X, ldx, 0, h->mx_B, c));
+  CK(h, mx_gemm(h, m, m, c, h->mx_B, c, 0, h->mx_B, c, 1, h->mx_H, m));
+  ProfScope ps(h, PK_EIG64, 13.3 * (double)m * m * m, 2.0 * m * m * sizeof(double2));
+  CK(h, launch_jacobi<double>(h->st, h->mx_H, m, h->mx_V, h->mx_w, h->mx_ctl + slot, h->opts.eig_max_sweeps,
+                              h->opts.barrier_timeout_s, h->num_sms));
+  return MPO_OK;
+}
+
+static int msvd_select(mpo_ctx* h, double2* X, int r, int c, int ldx, int cap, bool disc, double* S, double* sch, int* k) {
+  const int m = std::min(r, cap + h->mx_over);
+  if (m > h->mx_mcap || r > h->m_cap) return fail(h, MPO_ERR_STATE, "mixed factorisation larger than its workspace");
+  const int steps = m < r ? std::min(h->mx_steps, 7) : 0;
+  CK(h, cudaMemsetAsync(h->mx_chst, 0, sizeof(int), h->st));
+  // 1. FP32 copy and FP32 one-sided Jacobi SVD; the squared norm of X (the
+  // total weight of the discarded-weight ratio) before X is overwritten
+  {
+    ProfScope ps(h, PK_CONVERT, 0.0, (double)r * c * (2 * sizeof(double2) + sizeof(float2)));
+    to_fp32_kernel<<<grid_for((size_t)r * c, h->num_sms), 256, 0, h->st>>>(X, r, c, ldx, h->mx_a32);
+    frob2_kernel<<<1, 1024, 0, h->st>>>(X, r, c, ldx, h->scal + 2);
+    CK(h, cudaGetLastError());
+  }
+  {
+    const double mn = r, mx = c;
+    ProfScope ps(h, disc ? PK_SVD : PK_SVD_SWEEP, 4.0 * mn * mn * mx + 13.3 * mn * mn * mn,
+                 (2.0 * r * c + (double)r * r) * sizeof(float2));
+    if (h->block_min_rows > 0 && r >= h->block_min_rows)
+      CK(h, launch_block_jacobi<float>(h->st, h->mx_a32, r, c, c, h->mx_ut32, h->mx_w32, (float2*)h->bj_gpart,
+                                       h->bj_slots, (float2*)h->bj_j, h->bj_act, h->bj_act_ints, h->osctl,
+                                       h->opts.eig_max_sweeps, h->opts.barrier_timeout_s, h->num_sms));
+    else
+      CK(h, launch_onesided<float>(h->st, h->mx_a32, r, c, c, h->mx_ut32, h->mx_w32, h->osctl, h->opts.eig_max_sweeps,
+                                   h->opts.barrier_timeout_s, h->num_sms));
+  }
+  // 2. the m leading FP32 left singular vectors -> Q (FP64), orthonormalised
+  {
+    ProfScope ps(h, PK_SELECT, 0.0, (double)r * (sizeof(float) + sizeof(int) + sizeof(double)));
+    CK(h, launch_select<float>(h->st, h->mx_w32, r, m, -1.0, h->mx_perm32, h->mx_lam32, h->mx_info32, nullptr,
+                               nullptr, nullptr, nullptr));
+  }
+  {
+    ProfScope ps(h, PK_CONVERT, 0.0, (double)r * m * (sizeof(double2) + sizeof(float2)));
+    promote_columns_kernel<<<grid_for((size_t)r * m, h->num_sms), 256, 0, h->st>>>(h->mx_ut32, r, h->mx_perm32, m, h->mx_Q);
+    CK(h, cudaGetLastError());
+  }
+  int rc = mx_orthonormalise(h, r, m);
+  if (rc) return rc;
+  // 3. subspace iteration in FP64: Q <- orth(X X^H Q)
+  for (int it = 0; it < steps; ++it) {
+    CK(h, mx_gemm(h, c, m, r, X, ldx, 1, h->mx_Q, m, 0, h->mx_T, m));     // T = X^H Q (c x m)
+    CK(h, mx_gemm(h, r, m, c, X, ldx, 0, h->mx_T, m, 0, h->mx_Q2, m));    // X T (r x m)
+    std::swap(h->mx_Q, h->mx_Q2);
+    rc = mx_scholqr3(h, h->mx_Q, r, m);
+    if (rc) return rc;
+  }
+  // 4. Rayleigh-Ritz projection and the outputs in the one-sided Jacobi convention
+  rc = mx_ritz(h, X, r, c, ldx, m, 0);
+  if (rc) return rc;
+  CK(h, mx_gemm(h, m, r, m, h->mx_V, m, 1, h->mx_Q, m, 1, (double2*)h->vecs, r));   // V^H Q^H
+  CK(h, mx_gemm(h, m, c, m, h->mx_V, m, 1, h->mx_B, c, 0, X, ldx));                   // V^H B
+  h->vecs_conj = true;
+  {
+    ProfScope ps(h, PK_SELECT, 0.0, (double)m * (sizeof(double) + sizeof(int) + sizeof(double)));
+    CK(h, launch_select<double>(h->st, h->mx_w, m, cap, h->cutoff * h->cutoff, h->perm, h->lam2, h->info,
+                                disc ? h->scal + 1 : nullptr, h->scal, S, sch, m < r ? h->scal + 2 : nullptr));
+  }
+  CK(h, cudaMemcpyAsync(&h->hs->info, h->info, sizeof(SelectInfo), cudaMemcpyDeviceToHost, h->st));
+  CK(h, cudaMemcpyAsync(&h->hs->ctl, &h->osctl->g, sizeof(GridCtl), cudaMemcpyDeviceToHost, h->st));
+  CK(h, cudaMemcpyAsync(h->hs->eig, h->mx_ctl, sizeof(GridCtl), cudaMemcpyDeviceToHost, h->st));
+  CK(h, cudaMemcpyAsync(&h->hs->chol_status, h->mx_chst, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  if (h->prof) CK(h, cudaMemcpyAsync(h->hs->phase_ns, h->osctl->phase_ns, sizeof(h->hs->phase_ns), cudaMemcpyDeviceToHost, h->st));
+  CK(h, cudaStreamSynchronize(h->st));
+  if (h->prof) for (int i = 0; i < 3; ++i) h->prof_phase_ns[i] += h->hs->phase_ns[i];
+  if (h->hs->ctl.err) return fail(h, MPO_ERR_TIMEOUT, "grid barrier wait timed out in the FP32 SVD");
+  h->last_sweeps = h->hs->ctl.sweeps;
+  h->prof_sweeps += h->prof ? h->hs->ctl.sweeps : 0;
+  if (h->hs->ctl.status)
+    return fail(h, MPO_ERR_NOCONV, "FP32 Jacobi SVD reached eig_max_sweeps (" + std::to_string(r) + " x " + std::to_string(c) + ")");
+  if (h->hs->eig[0].err) return fail(h, MPO_ERR_TIMEOUT, "grid barrier wait timed out in the FP64 eigen-solve");
+  if (h->hs->eig[0].status)
+    return fail(h, MPO_ERR_NOCONV, "FP64 eigen-solve reached eig_max_sweeps (m = " + std::to_string(m) + ")");
+  if (h->hs->chol_status)
+    return fail(h, MPO_ERR_NOCONV, "Cholesky QR met a non-positive pivot (m = " + std::to_string(m) + ")");
+  *k = h->hs->info.k;
+  return MPO_OK;
+}
+
 // One-sided Jacobi SVD of X (r x c, rows orthogonalised in place; left factor
 // transposed in h->vecs), then select the kept squared singular values; waits
 // for the stream and returns the kept count in *k (or an error code).
 template <typename T>
 static int svd_select(mpo_ctx* h, cplx<T>* X, int r, int c, int ldx, int cap, bool disc, double* S, double* sch, int* k) {
+  if constexpr (std::is_same<T, double>::value) {
+    if (h->mixed) return msvd_select(h, X, r, c, ldx, cap, disc, S, sch, k);
+  }
+  h->vecs_conj = false;
   T* w = (T*)h->wv;
   {
     // algorithmic work of the factorisation: Hermitian Gram of the short side
@@ -408,7 +635,7 @@ static int move_right(mpo_ctx* h, int k) {
   if (rc) return rc;
   CK(h, gather_rows<T>(h, Y, mX, mX, rk, 1, 1, 1, (cplx<T>*)h->spare, rk));     // Q (mX x rk)
   swap_spare(h, k);
-  CK(h, gather_rows<T>(h, (cplx<T>*)h->vecs, r, r, rk, 0, 1, 2, tmp, r));         // R (rk x r)
+  CK(h, gather_rows<T>(h, (cplx<T>*)h->vecs, r, r, rk, 0, 1 ^ (int)h->vecs_conj, 2, tmp, r));   // R (rk x r)
   CK(h, gemm_p<T>(h, rk, mR, r, tmp, r, 0, S_<T>(h, k + 1), mR, 0, (cplx<T>*)h->spare, mR));
   swap_spare(h, k + 1);
   h->chi[k + 1] = rk;
@@ -432,7 +659,7 @@ static int move_left(mpo_ctx* h, int k, bool record) {
   if (rc) return rc;
   CK(h, gather_rows<T>(h, Y, mR, mR, rk, 0, 0, 1, (cplx<T>*)h->spare, mR));        // Lambda^-1 X'
   swap_spare(h, k);
-  CK(h, gather_rows<T>(h, (cplx<T>*)h->vecs, r, r, rk, 1, 0, 2, tmp, rk));          // U Lambda / ||kept||
+  CK(h, gather_rows<T>(h, (cplx<T>*)h->vecs, r, r, rk, 1, (int)h->vecs_conj, 2, tmp, rk));   // U Lambda / ||kept||
   CK(h, gemm_p<T>(h, mL, rk, r, S_<T>(h, k - 1), r, 0, tmp, rk, 0, (cplx<T>*)h->spare, rk));
   swap_spare(h, k - 1);
   h->chi[k] = rk;
@@ -472,7 +699,7 @@ static int gate_update(mpo_ctx* h, int i, const cplx<T>* M) {
     // theta' = U X', rows of X' = Lambda W^H
     rc = svd_select<T>(h, th, mL, mR, mR, h->chi_max, true, nullptr, nullptr, &k);
     if (rc) return rc;
-    CK(h, gather_rows<T>(h, (cplx<T>*)h->vecs, mL, mL, k, 1, 0, 0, A0, k));     // U_k -> site i
+    CK(h, gather_rows<T>(h, (cplx<T>*)h->vecs, mL, mL, k, 1, (int)h->vecs_conj, 0, A0, k));   // U_k -> site i
     CK(h, gather_rows<T>(h, th, mR, mR, k, 0, 0, 3, A1, mR));                    // Lambda W^H / ||kept||
   } else {
     // theta'^H = U X'  =>  theta' = X'^H U^H
@@ -480,7 +707,7 @@ static int gate_update(mpo_ctx* h, int i, const cplx<T>* M) {
     CK(h, conj_transpose<T>(h, th, mL, mR, mR, Y, mL));
     rc = svd_select<T>(h, Y, mR, mL, mL, h->chi_max, true, nullptr, nullptr, &k);
     if (rc) return rc;
-    CK(h, gather_rows<T>(h, (cplx<T>*)h->vecs, mR, mR, k, 0, 1, 2, A1, mR));    // Lambda U^H / ||kept||
+    CK(h, gather_rows<T>(h, (cplx<T>*)h->vecs, mR, mR, k, 0, 1 ^ (int)h->vecs_conj, 2, A1, mR));   // Lambda U^H / ||kept||
     CK(h, gather_rows<T>(h, Y, mL, mL, k, 1, 1, 1, A0, k));                      // X'^H Lambda^-1
   }
   h->chi[i + 1] = k;
@@ -658,6 +885,8 @@ void mpo_default_opts(mpo_opts* o) {
   o->barrier_timeout_s = 5.0;
   o->block_jacobi_min_rows = 0;
   o->tensor_cores = 0;
+  o->oversample = 0;
+  o->refine_steps = 0;
 }
 
 const char* mpo_version(void) { return "gb300-mpo 0.1 (sm_103a)"; }
@@ -668,12 +897,67 @@ static int init_fail(mpo_ctx* h, int code, const std::string& m) {
   return code;
 }
 
+// Device allocation that counts towards the handle's bytes.
+static bool ws_alloc(mpo_ctx* h, void** p, size_t bytes) {
+  if (cudaMalloc(p, std::max<size_t>(bytes, 256)) != cudaSuccess) { cudaGetLastError(); *p = nullptr; return false; }
+  h->bytes += bytes;
+  return true;
+}
+
+// Workspace of the factorisations (svd_select / msvd_select) for matrices of
+// at most m rows and ccap columns: left factor, values, selection, control
+// blocks, the block Jacobi's partial Grams and rotations, and for the
+// precision form its FP32 copy and FP64 refinement buffers.
+static bool alloc_factor_ws(mpo_ctx* h, int m, int ccap, size_t bj_nch) {
+  auto alloc = [&](void** p, size_t bytes) -> bool { return ws_alloc(h, p, bytes); };
+  const size_t rsz = h->prec != MPO_FP32 ? sizeof(double) : sizeof(float);
+  const size_t bj_pairs = (size_t)((m + JB - 1) / JB + 1) / 2 + 1;
+  bool ok = true;
+  ok = ok && alloc(&h->vecs, (size_t)m * m * h->esz);
+  ok = ok && alloc(&h->wv, (size_t)m * rsz);
+  ok = ok && alloc((void**)&h->perm, (size_t)m * sizeof(int));
+  ok = ok && alloc((void**)&h->lam2, (size_t)m * sizeof(double));
+  ok = ok && alloc((void**)&h->info, sizeof(SelectInfo));
+  ok = ok && alloc((void**)&h->ctl, sizeof(GridCtl));
+  ok = ok && alloc((void**)&h->osctl, sizeof(OSCtl));
+  ok = ok && alloc((void**)&h->tc_status, sizeof(int));
+  if (h->block_min_rows > 0) {
+    h->bj_slots = bj_pairs * bj_nch;
+    ok = ok && alloc(&h->bj_gpart, h->bj_slots * JP * JP * h->esz);
+    ok = ok && alloc(&h->bj_j, bj_pairs * JP * JP * h->esz);
+    h->bj_act_ints = bj_state_ints(m);
+    ok = ok && alloc((void**)&h->bj_act, h->bj_act_ints * sizeof(int));
+  }
+  if (h->mixed) {
+    const size_t mm = (size_t)h->mx_mcap;
+    ok = ok && alloc((void**)&h->mx_a32, (size_t)m * ccap * sizeof(float2));
+    ok = ok && alloc((void**)&h->mx_ut32, (size_t)m * m * sizeof(float2));
+    ok = ok && alloc((void**)&h->mx_w32, (size_t)m * sizeof(float));
+    ok = ok && alloc((void**)&h->mx_perm32, (size_t)m * sizeof(int));
+    ok = ok && alloc((void**)&h->mx_lam32, (size_t)m * sizeof(double));
+    ok = ok && alloc((void**)&h->mx_info32, sizeof(SelectInfo));
+    ok = ok && alloc((void**)&h->mx_Q, (size_t)m * mm * sizeof(double2));
+    ok = ok && alloc((void**)&h->mx_Q2, (size_t)m * mm * sizeof(double2));
+    ok = ok && alloc((void**)&h->mx_B, (size_t)ccap * mm * sizeof(double2));
+    ok = ok && alloc((void**)&h->mx_T, (size_t)ccap * mm * sizeof(double2));
+    ok = ok && alloc((void**)&h->mx_H, mm * mm * sizeof(double2));
+    ok = ok && alloc((void**)&h->mx_V, mm * mm * sizeof(double2));
+    ok = ok && alloc((void**)&h->mx_G, mm * mm * sizeof(double2));
+    ok = ok && alloc((void**)&h->mx_w, mm * sizeof(double));
+    ok = ok && alloc((void**)&h->mx_ctl, 8 * sizeof(GridCtl));
+    ok = ok && alloc((void**)&h->mx_linv, (mm / CHOL_NB + 1) * CHOL_NB * CHOL_NB * sizeof(double2));
+    ok = ok && alloc((void**)&h->mx_ptmp, (size_t)std::max<size_t>(m, mm) * CHOL_NB * sizeof(double2));
+    ok = ok && alloc((void**)&h->mx_chst, sizeof(int));
+  }
+  return ok;
+}
+
 int mpo_init(mpo_handle* out, int n, int chi_max, mpo_precision prec, void* stream, const mpo_opts* opts) {
   if (!out) { g_last_init_error = "out is NULL"; return MPO_ERR_ARG; }
   *out = nullptr;
   if (n < 2 || n % 2 || n > 4096) { g_last_init_error = "n_qubits must be even, 2..4096"; return MPO_ERR_ARG; }
   if (chi_max < 1 || chi_max > 4096) { g_last_init_error = "chi_max must be 1..4096"; return MPO_ERR_ARG; }
-  if (prec != MPO_FP64 && prec != MPO_FP32) { g_last_init_error = "unknown precision"; return MPO_ERR_ARG; }
+  if (prec != MPO_FP64 && prec != MPO_FP32 && prec != MPO_MIXED_FP32) { g_last_init_error = "unknown precision"; return MPO_ERR_ARG; }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
     cudaGetLastError();
@@ -689,15 +973,17 @@ int mpo_init(mpo_handle* out, int n, int chi_max, mpo_precision prec, void* stre
   if (opts) h->opts = *opts;
   if (h->opts.eig_max_sweeps <= 0) h->opts.eig_max_sweeps = 40;
   if (!(h->opts.barrier_timeout_s > 0.0)) h->opts.barrier_timeout_s = 5.0;
-  h->cutoff = h->opts.sv_rel_cutoff > 0.0 ? h->opts.sv_rel_cutoff : (prec == MPO_FP64 ? 1e-12 : 1e-6);
+  h->mixed = prec == MPO_MIXED_FP32;
+  h->cutoff = h->opts.sv_rel_cutoff > 0.0 ? h->opts.sv_rel_cutoff
+                                          : (prec == MPO_FP64 ? 1e-12 : (h->mixed ? 1e-7 : 1e-6));
   if (cudaGetDevice(&h->device) != cudaSuccess) return init_fail(h, MPO_ERR_CUDA, "cudaGetDevice failed");
   cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
   int coop = 0;
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
   if (!coop) return init_fail(h, MPO_ERR_CUDA, "device lacks cooperative launch");
 
-  h->esz = prec == MPO_FP64 ? sizeof(double2) : sizeof(float2);
-  const size_t rsz = prec == MPO_FP64 ? sizeof(double) : sizeof(float);
+  h->esz = prec != MPO_FP32 ? sizeof(double2) : sizeof(float2);
+  const size_t rsz = prec != MPO_FP32 ? sizeof(double) : sizeof(float);
   h->cap.resize(n + 1);
   for (int b = 0; b <= n; ++b) h->cap[b] = cap_of(b, n, chi_max);
   h->chi.assign(n + 1, 1);
@@ -712,56 +998,52 @@ int mpo_init(mpo_handle* out, int n, int chi_max, mpo_precision prec, void* stre
   for (int b = 0; b <= n; ++b) m = std::max(m, h->cap[b]);
   h->theta_cap = th;
   h->m_cap = m;
-  const int jac_limit = prec == MPO_FP64 ? 8192 : 16384;   // rotation table must fit shared memory
+  const int jac_limit = prec != MPO_FP32 ? 8192 : 16384;   // rotation table must fit shared memory
   if (m > jac_limit) return init_fail(h, MPO_ERR_ARG, "bond dimension too large for the eigen-solver's shared-memory table");
   h->tmp_cap = (size_t)m * chi_max;
   h->tensor_cores = prec == MPO_FP32 && h->opts.tensor_cores > 0;
   h->block_min_rows = h->opts.block_jacobi_min_rows < 0 ? 0
-                      : (h->opts.block_jacobi_min_rows > 0 ? h->opts.block_jacobi_min_rows : (prec == MPO_FP32 ? 64 : 0));
-  const size_t bj_pairs = (size_t)((m + JB - 1) / JB + 1) / 2 + 1;
+                      : (h->opts.block_jacobi_min_rows > 0 ? h->opts.block_jacobi_min_rows : (prec != MPO_FP64 ? 64 : 0));
+  // precision form: FP32 approximate SVD with oversampling, FP64 refinement
+  h->mx_over = h->opts.oversample > 0 ? h->opts.oversample : (h->opts.oversample < 0 ? 0 : chi_max);
+  h->mx_steps = h->opts.refine_steps > 0 ? std::min(h->opts.refine_steps, 7) : (h->opts.refine_steps < 0 ? 0 : 5);
+  h->mx_mcap = std::min(m, chi_max + h->mx_over);
+  int mx_ccap = 1;   // longest row of a factorised matrix
+  for (int i = 0; i + 1 < n; ++i) mx_ccap = std::max(mx_ccap, 4 * std::max(h->cap[i], h->cap[i + 2]));
+  for (int b = 0; b + 1 <= n; ++b) mx_ccap = std::max(mx_ccap, 4 * h->cap[std::min(b + 1, n)]);
   const size_t bj_nch = (size_t)(4 * chi_max + JCW - 1) / JCW + 1;
   const int ngmax = n / 2;
   const size_t need = (size_t)(n + 1) * h->site_cap * h->esz + 2 * th * h->esz + (size_t)m * m * h->esz +
                       h->tmp_cap * h->esz + (size_t)m * (rsz + sizeof(int) + sizeof(double)) +
                       (size_t)ngmax * 256 * h->esz + (size_t)ngmax * (16 * sizeof(double2) + sizeof(double)) +
-                      (size_t)(n - 1) * (1 + chi_max) * sizeof(double) + 2 * (size_t)chi_max * sizeof(double2) + 4096;
+                      (size_t)(n - 1) * (1 + chi_max) * sizeof(double) + 2 * (size_t)chi_max * sizeof(double2) + 4096 +
+                      (h->mixed ? (size_t)m * mx_ccap * sizeof(float2) + (size_t)m * m * sizeof(float2) +
+                                      (size_t)m * (sizeof(float) + sizeof(int) + sizeof(double)) +
+                                      2 * (size_t)m * h->mx_mcap * sizeof(double2) +
+                                      2 * (size_t)mx_ccap * h->mx_mcap * sizeof(double2) +
+                                      4 * (size_t)h->mx_mcap * h->mx_mcap * sizeof(double2) +
+                                      (size_t)std::max(m, h->mx_mcap) * CHOL_NB * sizeof(double2) +
+                                      (size_t)h->mx_mcap * sizeof(double)
+                                : 0);
   if (h->opts.arena_cap_bytes > 0 && need > h->opts.arena_cap_bytes)
     return init_fail(h, MPO_ERR_OOM, "device memory needed (" + std::to_string(need) + " B) exceeds arena_cap_bytes");
   size_t freeb = 0, totb = 0;
   if (cudaMemGetInfo(&freeb, &totb) == cudaSuccess && need > freeb)
     return init_fail(h, MPO_ERR_OOM, "device memory needed (" + std::to_string(need) + " B) exceeds free memory");
 
-  auto alloc = [&](void** p, size_t bytes) -> bool {
-    if (cudaMalloc(p, std::max<size_t>(bytes, 256)) != cudaSuccess) { cudaGetLastError(); *p = nullptr; return false; }
-    h->bytes += bytes;
-    return true;
-  };
+  auto alloc = [&](void** p, size_t bytes) -> bool { return ws_alloc(h, p, bytes); };
   h->site.assign(n, nullptr);
   bool ok = true;
   for (int k = 0; k < n && ok; ++k) ok = alloc(&h->site[k], h->site_cap * h->esz);
   ok = ok && alloc(&h->spare, h->site_cap * h->esz);
   ok = ok && alloc(&h->theta, th * h->esz);
   ok = ok && alloc(&h->theta2, th * h->esz);
-  ok = ok && alloc(&h->vecs, (size_t)m * m * h->esz);
   ok = ok && alloc(&h->tmp, h->tmp_cap * h->esz);
-  ok = ok && alloc(&h->wv, (size_t)m * rsz);
-  ok = ok && alloc((void**)&h->perm, (size_t)m * sizeof(int));
-  ok = ok && alloc((void**)&h->lam2, (size_t)m * sizeof(double));
   ok = ok && alloc(&h->Ms, (size_t)std::max(1, ngmax) * 256 * h->esz);
   ok = ok && alloc((void**)&h->dgates, (size_t)std::max(1, ngmax) * 16 * sizeof(double2));
   ok = ok && alloc((void**)&h->dp, (size_t)std::max(1, ngmax) * sizeof(double));
   ok = ok && alloc((void**)&h->dsup, 256 * sizeof(double2));
-  ok = ok && alloc((void**)&h->info, sizeof(SelectInfo));
-  ok = ok && alloc((void**)&h->ctl, sizeof(GridCtl));
-  ok = ok && alloc((void**)&h->osctl, sizeof(OSCtl));
-  ok = ok && alloc((void**)&h->tc_status, sizeof(int));
-  if (h->block_min_rows > 0) {
-    h->bj_slots = bj_pairs * bj_nch;
-    ok = ok && alloc(&h->bj_gpart, h->bj_slots * JP * JP * h->esz);
-    ok = ok && alloc(&h->bj_j, bj_pairs * JP * JP * h->esz);
-    h->bj_act_ints = bj_state_ints(m);
-    ok = ok && alloc((void**)&h->bj_act, h->bj_act_ints * sizeof(int));
-  }
+  ok = ok && alloc_factor_ws(h, m, mx_ccap, bj_nch);
   ok = ok && alloc((void**)&h->scal, 4 * sizeof(double));
   ok = ok && alloc((void**)&h->dS, (size_t)(n - 1) * sizeof(double));
   ok = ok && alloc((void**)&h->dschmidt, (size_t)(n - 1) * chi_max * sizeof(double));
@@ -775,7 +1057,7 @@ int mpo_init(mpo_handle* out, int n, int chi_max, mpo_precision prec, void* stre
   }
   // product state |0..0><0..0|: every site 1 x 4 x 1 with A[0][0][0] = 1 (Sec. 4.1)
   std::vector<unsigned char> one(h->esz, 0);
-  if (prec == MPO_FP64) { double v = 1.0; memcpy(one.data(), &v, sizeof v); }
+  if (prec != MPO_FP32) { double v = 1.0; memcpy(one.data(), &v, sizeof v); }
   else { float v = 1.0f; memcpy(one.data(), &v, sizeof v); }
   for (int k = 0; k < n; ++k) {
     if (cudaMemsetAsync(h->site[k], 0, 4 * h->esz, h->st) != cudaSuccess ||
@@ -807,7 +1089,10 @@ void mpo_free(mpo_handle h) {
   if (h->batch) { batch_free(h); return; }
   for (void* p : h->site) if (p) cudaFree(p);
   void* ps[] = {h->spare, h->theta, h->theta2, h->osctl, h->tc_status, h->bj_gpart, h->bj_j, h->bj_act, h->vecs, h->tmp, h->wv, h->perm, h->lam2, h->Ms, h->dgates,
-                h->dsup, h->dp, h->info, h->ctl, h->scal, h->dS, h->dschmidt, h->tv0, h->tv1};
+                h->dsup, h->dp, h->info, h->ctl, h->scal, h->dS, h->dschmidt, h->tv0, h->tv1,
+                h->mx_a32, h->mx_ut32, h->mx_w32, h->mx_perm32, h->mx_lam32, h->mx_info32, h->mx_Q, h->mx_Q2,
+                h->mx_B, h->mx_T, h->mx_H, h->mx_V, h->mx_G, h->mx_w, h->mx_ctl,
+                h->mx_linv, h->mx_ptmp, h->mx_chst};
   for (void* p : ps) if (p) cudaFree(p);
   if (h->hs) cudaFreeHost(h->hs);
   for (auto& q : h->pend) { cudaEventDestroy(q.a); cudaEventDestroy(q.b); }
@@ -836,14 +1121,14 @@ int mpo_apply_layer(mpo_handle h, int parity, const double* gates, const double*
   if (parity != 0 && parity != 1) return fail(h, MPO_ERR_ARG, "parity must be 0 or 1");
   const int ng = (h->n - parity) / 2;
   if (ng > 0 && (!gates || !p || p_stride < 0)) return fail(h, MPO_ERR_ARG, "gates/p must be non-NULL, p_stride >= 0");
-  return h->prec == MPO_FP64 ? apply_layer_t<double>(h, parity, gates, p, p_stride)
+  return dsite(h) ? apply_layer_t<double>(h, parity, gates, p, p_stride)
                              : apply_layer_t<float>(h, parity, gates, p, p_stride);
 }
 
 int mpo_apply_gate(mpo_handle h, int bond, const double* gate, double p) {
   GUARD(h);
   if (bond < 0 || bond > h->n - 2 || !gate) return fail(h, MPO_ERR_ARG, "bad bond or gate");
-  if (h->prec == MPO_FP64) {
+  if (dsite(h)) {
     int rc = stage_gates<double>(h, 1, gate, &p, 0);
     return rc ? rc : gate_update<double>(h, bond, (const double2*)h->Ms);
   }
@@ -859,16 +1144,16 @@ int mpo_apply_superop(mpo_handle h, int bond, const double* M) {
     CK(h, cudaMemcpyAsync(h->dsup, M, sizeof(double2) * 256, cudaMemcpyHostToDevice, h->st));
     src = h->dsup;
   }
-  if (h->prec == MPO_FP64) cast_superop_kernel<double><<<1, 256, 0, h->st>>>(src, (double2*)h->Ms);
+  if (dsite(h)) cast_superop_kernel<double><<<1, 256, 0, h->st>>>(src, (double2*)h->Ms);
   else cast_superop_kernel<float><<<1, 256, 0, h->st>>>(src, (float2*)h->Ms);
   CK(h, cudaGetLastError());
-  return h->prec == MPO_FP64 ? gate_update<double>(h, bond, (const double2*)h->Ms)
+  return dsite(h) ? gate_update<double>(h, bond, (const double2*)h->Ms)
                              : gate_update<float>(h, bond, (const float2*)h->Ms);
 }
 
 int mpo_sweep(mpo_handle h) {
   GUARD(h);
-  return h->prec == MPO_FP64 ? sweep_all<double>(h) : sweep_all<float>(h);
+  return dsite(h) ? sweep_all<double>(h) : sweep_all<float>(h);
 }
 
 int mpo_entropy(mpo_handle h, double* S, double* trace, double* discarded) {
@@ -882,7 +1167,7 @@ int mpo_entropy(mpo_handle h, double* S, double* trace, double* discarded) {
   for (int b = 0; b < h->n - 1; ++b) S[b] = h->s_valid[b] ? hS[b] : NAN;
   if (discarded) *discarded = disc;
   if (trace) {
-    int rc = h->prec == MPO_FP64 ? trace_t<double>(h, trace) : trace_t<float>(h, trace);
+    int rc = dsite(h) ? trace_t<double>(h, trace) : trace_t<float>(h, trace);
     if (rc) return rc;
   }
   return MPO_OK;
@@ -923,7 +1208,7 @@ int mpo_probability(mpo_handle h, int n_strings, const unsigned char* bits, doub
   if (n_strings < 1 || !bits || !P) return fail(h, MPO_ERR_ARG, "mpo_probability: bad arguments");
   for (size_t i = 0; i < (size_t)n_strings * h->n; ++i)
     if (bits[i] > 1) return fail(h, MPO_ERR_ARG, "mpo_probability: bits must be 0 or 1");
-  return h->prec == MPO_FP64 ? chain_t<double>(h, n_strings, nullptr, const_cast<unsigned char*>(bits), P)
+  return dsite(h) ? chain_t<double>(h, n_strings, nullptr, const_cast<unsigned char*>(bits), P)
                              : chain_t<float>(h, n_strings, nullptr, const_cast<unsigned char*>(bits), P);
 }
 
@@ -932,7 +1217,7 @@ int mpo_sample(mpo_handle h, int n_samples, const double* uniforms, unsigned cha
   if (n_samples < 1 || !uniforms || !bits) return fail(h, MPO_ERR_ARG, "mpo_sample: bad arguments");
   for (size_t i = 0; i < (size_t)n_samples * h->n; ++i)
     if (!(uniforms[i] >= 0.0 && uniforms[i] < 1.0)) return fail(h, MPO_ERR_ARG, "mpo_sample: uniforms must lie in [0, 1)");
-  return h->prec == MPO_FP64 ? chain_t<double>(h, n_samples, uniforms, bits, P)
+  return dsite(h) ? chain_t<double>(h, n_samples, uniforms, bits, P)
                              : chain_t<float>(h, n_samples, uniforms, bits, P);
 }
 
@@ -979,7 +1264,7 @@ int mpo_get_site(mpo_handle h, int k, double* buf, int* chiL, int* chiR) {
   const size_t cnt = (size_t)h->chi[k] * 4 * h->chi[k + 1];
   double ln = 0.0;
   CK(h, cudaMemcpyAsync(&ln, h->scal, sizeof(double), cudaMemcpyDeviceToHost, h->st));
-  if (h->prec == MPO_FP64) {
+  if (dsite(h)) {
     CK(h, cudaMemcpyAsync(buf, h->site[k], cnt * sizeof(double2), cudaMemcpyDeviceToHost, h->st));
     CK(h, cudaStreamSynchronize(h->st));
   } else {
@@ -1038,7 +1323,7 @@ int mpo_svd_last_stats(int* sweeps, double* phase_ms3) {
 }
 
 int mpo_svd(int r, int c, void* X, void* w, void* Ut, mpo_precision prec, int max_sweeps, int block, void* stream) {
-  if (r < 1 || c < 1 || !X || !w || !Ut) return MPO_ERR_ARG;
+  if (r < 1 || c < 1 || !X || !w || !Ut || (prec != MPO_FP64 && prec != MPO_FP32)) return MPO_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return MPO_ERR_CUDA;
@@ -1078,6 +1363,64 @@ int mpo_svd(int r, int c, void* X, void* w, void* Ut, mpo_precision prec, int ma
   if (hc.err) return MPO_ERR_TIMEOUT;
   if (hc.status) return MPO_ERR_NOCONV;
   return MPO_OK;
+}
+
+int mpo_svd_truncated(int r, int c, const void* A, int cap, mpo_precision prec, const mpo_opts* opts, void* U,
+                      void* X, double* lam2, int* k, void* stream) {
+  if (r < 1 || c < 1 || r > c || cap < 1 || !A || !U || !X || !lam2 || !k ||
+      (prec != MPO_FP64 && prec != MPO_FP32 && prec != MPO_MIXED_FP32)) {
+    g_last_init_error = "mpo_svd_truncated: bad argument (needs 1 <= r <= c, cap >= 1, non-NULL buffers)";
+    return MPO_ERR_ARG;
+  }
+  if (r > 8192) { g_last_init_error = "mpo_svd_truncated: r > 8192"; return MPO_ERR_ARG; }
+  mpo_ctx* h = new mpo_ctx();
+  h->n = 2;
+  h->chi_max = cap;
+  h->prec = prec;
+  h->st = (cudaStream_t)stream;
+  mpo_default_opts(&h->opts);
+  if (opts) h->opts = *opts;
+  if (h->opts.eig_max_sweeps <= 0) h->opts.eig_max_sweeps = 40;
+  if (!(h->opts.barrier_timeout_s > 0.0)) h->opts.barrier_timeout_s = 5.0;
+  h->mixed = prec == MPO_MIXED_FP32;
+  h->cutoff = h->opts.sv_rel_cutoff > 0.0 ? h->opts.sv_rel_cutoff : (prec == MPO_FP64 ? 1e-12 : (h->mixed ? 1e-7 : 1e-6));
+  h->esz = prec != MPO_FP32 ? sizeof(double2) : sizeof(float2);
+  if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return MPO_ERR_CUDA; }
+  cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+  h->m_cap = r;
+  h->block_min_rows = h->opts.block_jacobi_min_rows < 0 ? 0
+                      : (h->opts.block_jacobi_min_rows > 0 ? h->opts.block_jacobi_min_rows : (prec != MPO_FP64 ? 64 : 0));
+  h->mx_over = h->opts.oversample > 0 ? h->opts.oversample : (h->opts.oversample < 0 ? 0 : cap);
+  h->mx_steps = h->opts.refine_steps > 0 ? std::min(h->opts.refine_steps, 7) : (h->opts.refine_steps < 0 ? 0 : 5);
+  h->mx_mcap = std::min(r, cap + h->mx_over);
+  const size_t nch = (size_t)(c + JCW - 1) / JCW + 1;
+  bool ok = ws_alloc(h, &h->theta, (size_t)r * c * h->esz) && alloc_factor_ws(h, r, c, nch) &&
+            ws_alloc(h, (void**)&h->scal, 4 * sizeof(double));
+  if (ok && cudaMallocHost((void**)&h->hs, sizeof(HostSync)) != cudaSuccess) { cudaGetLastError(); h->hs = nullptr; ok = false; }
+  if (!ok) { mpo_free(h); g_last_init_error = "mpo_svd_truncated: allocation failed"; return MPO_ERR_OOM; }
+  int rc = MPO_OK, kk = 0;
+  auto ck = [&](cudaError_t e) { if (rc == MPO_OK && e != cudaSuccess) { rc = MPO_ERR_CUDA; g_last_init_error = cudaGetErrorString(e); } };
+  ck(cudaMemcpyAsync(h->theta, A, (size_t)r * c * h->esz, cudaMemcpyDeviceToDevice, h->st));
+  ck(cudaMemsetAsync(h->scal, 0, 4 * sizeof(double), h->st));
+  if (rc == MPO_OK) {
+    rc = prec != MPO_FP32 ? svd_select<double>(h, (double2*)h->theta, r, c, c, cap, true, nullptr, nullptr, &kk)
+                          : svd_select<float>(h, (float2*)h->theta, r, c, c, cap, true, nullptr, nullptr, &kk);
+    if (rc) g_last_init_error = h->msg;
+  }
+  if (rc == MPO_OK) {
+    if (prec != MPO_FP32) {
+      ck(gather_rows<double>(h, (double2*)h->vecs, r, r, kk, 1, (int)h->vecs_conj, 0, (double2*)U, cap));
+      ck(gather_rows<double>(h, (double2*)h->theta, c, c, kk, 0, 0, 0, (double2*)X, c));
+    } else {
+      ck(gather_rows<float>(h, (float2*)h->vecs, r, r, kk, 1, 0, 0, (float2*)U, cap));
+      ck(gather_rows<float>(h, (float2*)h->theta, c, c, kk, 0, 0, 0, (float2*)X, c));
+    }
+    ck(cudaMemcpyAsync(lam2, h->lam2, sizeof(double) * kk, cudaMemcpyDeviceToHost, h->st));
+    ck(cudaStreamSynchronize(h->st));
+    *k = kk;
+  }
+  mpo_free(h);
+  return rc;
 }
 
 // ---------------------------------------------------------------------------
@@ -1171,7 +1514,7 @@ int mpo_svd_static(int r, int c, void* X, void* w, void* Ut, mpo_precision prec,
 
 int mpo_gemm(int M, int N, int K, const void* A, const void* B, void* C, mpo_precision prec, int tensor_cores,
              void* stream) {
-  if (M < 1 || N < 1 || K < 1 || !A || !B || !C) return MPO_ERR_ARG;
+  if (M < 1 || N < 1 || K < 1 || !A || !B || !C || (prec != MPO_FP64 && prec != MPO_FP32)) return MPO_ERR_ARG;
   if (tensor_cores && prec != MPO_FP32) return MPO_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e;
@@ -1194,7 +1537,7 @@ int mpo_gemm(int M, int N, int K, const void* A, const void* B, void* C, mpo_pre
 }
 
 int mpo_eigh(int m, void* A, void* w, void* V, mpo_precision prec, int max_sweeps, void* stream) {
-  if (m < 1 || !A || !w || !V) return MPO_ERR_ARG;
+  if (m < 1 || !A || !w || !V || (prec != MPO_FP64 && prec != MPO_FP32)) return MPO_ERR_ARG;
   const int lim = prec == MPO_FP64 ? 8192 : 16384;
   if (m > lim) return MPO_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;

@@ -13,7 +13,8 @@ import numpy as np
 
 from . import build as _build
 
-MPO_FP64, MPO_FP32 = 0, 1
+MPO_FP64, MPO_FP32, MPO_MIXED_FP32 = 0, 1, 2
+PRECISIONS = {"fp64": MPO_FP64, "fp32": MPO_FP32, "mixed": MPO_MIXED_FP32}
 MPO_S_ALL_BONDS, MPO_S_CENTRE = 0, 1
 ERRORS = {0: "MPO_OK", -1: "MPO_ERR_ARG", -2: "MPO_ERR_CUDA", -3: "MPO_ERR_OOM", -4: "MPO_ERR_NOCONV",
           -5: "MPO_ERR_TIMEOUT", -6: "MPO_ERR_STATE"}
@@ -22,7 +23,7 @@ EXPORTS = ["mpo_default_opts", "mpo_init", "mpo_apply_layer", "mpo_apply_gate", 
            "mpo_device_bytes", "mpo_free", "mpo_last_error", "mpo_eigh", "mpo_svd", "mpo_version",
            "mpo_profile", "mpo_profile_read", "mpo_profile_sweeps", "mpo_profile_phases", "mpo_svd_static",
            "mpo_probability", "mpo_sample", "mpo_gemm", "mpo_svd_last_stats",
-           "mpo_init_batch", "mpo_apply_layer_batch", "mpo_batch_instance"]
+           "mpo_init_batch", "mpo_apply_layer_batch", "mpo_batch_instance", "mpo_svd_truncated"]
 
 
 class MPOError(RuntimeError):
@@ -35,7 +36,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("eig_max_sweeps", ctypes.c_int), ("sv_rel_cutoff", ctypes.c_double),
                 ("arena_cap_bytes", ctypes.c_size_t), ("smode", ctypes.c_int),
                 ("barrier_timeout_s", ctypes.c_double), ("block_jacobi_min_rows", ctypes.c_int),
-                ("tensor_cores", ctypes.c_int)]
+                ("tensor_cores", ctypes.c_int), ("oversample", ctypes.c_int), ("refine_steps", ctypes.c_int)]
 
 
 _lib = None
@@ -83,6 +84,7 @@ def load_library(path: str | None = None):
         "mpo_init_batch": (I, [ctypes.POINTER(P), I, IP, I, I, P, ctypes.POINTER(Opts), I]),
         "mpo_apply_layer_batch": (I, [P, I, P, DP, IP, DP, DP, DP]),
         "mpo_batch_instance": (I, [P, I, ctypes.POINTER(P)]),
+        "mpo_svd_truncated": (I, [I, I, P, I, I, ctypes.POINTER(Opts), P, P, DP, IP, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -116,7 +118,7 @@ def default_opts() -> Opts:
 
 
 def _make_opts(cutoff=0.0, eig_max_sweeps=0, arena_cap_bytes=0, centre_only=False, barrier_timeout_s=0.0,
-               block_jacobi_min_rows=0, tensor_cores=False) -> Opts:
+               block_jacobi_min_rows=0, tensor_cores=False, oversample=0, refine_steps=0) -> Opts:
     o = default_opts()
     if cutoff > 0:
         o.sv_rel_cutoff = cutoff
@@ -128,6 +130,8 @@ def _make_opts(cutoff=0.0, eig_max_sweeps=0, arena_cap_bytes=0, centre_only=Fals
         o.barrier_timeout_s = barrier_timeout_s
     o.block_jacobi_min_rows = block_jacobi_min_rows
     o.tensor_cores = 1 if tensor_cores else 0
+    o.oversample = int(oversample)
+    o.refine_steps = int(refine_steps)
     return o
 
 
@@ -137,17 +141,17 @@ class MPO:
     def __init__(self, n: int, chi_max: int, precision: str = "fp64", *, cutoff: float = 0.0,
                  eig_max_sweeps: int = 0, arena_cap_bytes: int = 0, centre_only: bool = False,
                  barrier_timeout_s: float = 0.0, block_jacobi_min_rows: int = 0, tensor_cores: bool = False,
-                 stream=None, _borrowed=None):
+                 oversample: int = 0, refine_steps: int = 0, stream=None, _borrowed=None):
         lib = load_library()
         self._lib = lib
         self.n, self.chi_max = n, chi_max
-        self.prec = {"fp64": MPO_FP64, "fp32": MPO_FP32}[precision]
+        self.prec = PRECISIONS[precision]
         self._owned = _borrowed is None
         if _borrowed is not None:        # an instance of a batch: the batch owns it
             self.h = _borrowed
             return
         o = _make_opts(cutoff, eig_max_sweeps, arena_cap_bytes, centre_only, barrier_timeout_s,
-                       block_jacobi_min_rows, tensor_cores)
+                       block_jacobi_min_rows, tensor_cores, oversample, refine_steps)
         h = ctypes.c_void_p()
         st = ctypes.c_void_p(stream) if stream is not None else _current_stream()
         rc = lib.mpo_init(ctypes.byref(h), n, chi_max, self.prec, st, ctypes.byref(o))
@@ -291,7 +295,7 @@ class MPOBatch:
         self.k = len(self.n_list)
         self.chi_max = chi_max
         self.precision = precision
-        self.prec = {"fp64": MPO_FP64, "fp32": MPO_FP32}[precision]
+        self.prec = PRECISIONS[precision]
         self.offsets = np.concatenate([[0], np.cumsum([n - 1 for n in self.n_list])]).astype(np.int64)
         o = _make_opts(**opts)
         nn = np.ascontiguousarray(self.n_list, dtype=np.int32)
@@ -425,3 +429,26 @@ def gemm(A, B, precision: str = "fp32", tensor_cores: bool = True):
     if rc != 0:
         raise MPOError(rc, "mpo_gemm failed")
     return C
+
+
+def svd_truncated(A, cap: int, precision: str = "mixed", **opts):
+    """Truncated SVD of one matrix in the arithmetic of a precision form
+    (mpo_svd_truncated, test export). A: CUDA tensor (r, c), r <= c,
+    complex128 (fp64 / mixed) or complex64 (fp32); not modified. Returns
+    (U (r, k), X (k, c), lam2 (k,) numpy) with U X the kept part of A."""
+    import torch
+    lib = load_library()
+    r, c = A.shape
+    prec = PRECISIONS[precision]
+    U = torch.zeros((r, cap), dtype=A.dtype, device=A.device)
+    X = torch.zeros((cap, c), dtype=A.dtype, device=A.device)
+    lam2 = np.zeros(cap)
+    k = ctypes.c_int()
+    o = _make_opts(**opts)
+    rc = lib.mpo_svd_truncated(r, c, A.contiguous().data_ptr(), cap, prec, ctypes.byref(o), U.data_ptr(),
+                               X.data_ptr(), lam2.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(k),
+                               ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if rc != 0:
+        raise MPOError(rc, lib.mpo_last_error(None).decode())
+    kk = k.value
+    return U[:, :kk], X[:kk], lam2[:kk]
