@@ -49,9 +49,55 @@ WORKLOADS = {
 DEFAULT_WORKLOAD = "n64_chi1024_p0.005"
 METRIC = "noisy-gate MPO updates/s at chi=1024 (n=64 Haar brickwork, p=0.005)"
 
-# FP32 / FP64 SIMT peaks (flop/s) from the unit counts and the maximum SM clock:
-# 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz; FP64 the nominal 1.25 TFLOP/s.
-ALU_PEAK = {"fp32": 152 * 128 * 2 * 2.07e9, "fp64": 1.25e12}
+# FP64 and FP32 SIMT rates measured on this GPU model with an FMA-chain probe
+# (8 independent chains per thread, 152 x 8 CTAs of 256 threads, CUDA events):
+# the measured peaks file carries only the HBM copy and the BF16 GEMM rates.
+FP64_PROBE_TFLOPS = 1.20
+FP32_PROBE_TFLOPS = 74.6
+
+
+def load_peaks() -> dict:
+    """Roofline denominators: HBM copy and BF16 GEMM rates from the measured
+    peaks file (else the documented fallback), TF32 tensor = BF16 / 2 (the
+    nominal ratio), FP64 / FP32 SIMT from the probe above."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        hbm, bf16s, src = float(d["hbm_gbs"]), float(d["bf16_tflops_sustained"]), "measured"
+    except (OSError, KeyError, ValueError):
+        hbm, bf16s, src = 6800.0, 1700.0, "fallback"
+    return {"hbm_gbs": hbm, "bf16_tflops": bf16s, "tf32_tflops": bf16s / 2.0, "fp64_tflops": FP64_PROBE_TFLOPS,
+            "fp32_simt_tflops": FP32_PROBE_TFLOPS, "source": src}
+
+
+def step_work(dims, n: int, parity: int, chi: int, prec: str, over: int, centre_only: bool) -> dict:
+    """Algorithmic work of one brickwork step as the hot-path scope counts it
+    (real flops, complex multiply-add = 8), from the bond dimensions dims:
+    per gate theta 8 (4 chiL)(4 chiR) chiM, superoperator 2048 chiL chiR,
+    Hermitian Gram of theta' 4 r^2 c, projection to the kept right factor
+    8 k r c (r, c = the shorter and longer side of theta', k = min(chi, r)),
+    and the Hermitian eigen-solve 13.3 m^3 with m = min(r, chi + oversample)
+    (precision form) or m = r; per recorded bond of the Schmidt sweep a
+    chi_b x 4 chi_{b+1} factorisation, 12 r^2 c GEMM-class + 13.3 r^3. Bytes:
+    the four site tensors each gate reads or writes."""
+    esz = 8 if prec == "fp32" else 16
+    gemm = solve = byts = 0.0
+    for l in range(1 + parity, n, 2):
+        i = l - 1
+        cl, cm, cr = dims[i], dims[i + 1], dims[i + 2]
+        r, c = 4 * min(cl, cr), 4 * max(cl, cr)
+        k = min(chi, r)
+        gemm += 8.0 * (4 * cl) * (4 * cr) * cm + 2048.0 * cl * cr + 4.0 * r * r * c + 8.0 * k * r * c
+        m = min(r, chi + over) if prec == "mixed" else r
+        solve += 13.3 * m ** 3
+        byts += 2.0 * (cl * 4 * cm + cm * 4 * cr) * esz
+    bonds = [n // 2] if centre_only else range(1, n)
+    for b in bonds:
+        r, c = dims[b], 4 * dims[b + 1]
+        gemm += 12.0 * r * r * c
+        solve += 13.3 * r ** 3
+    return {"gemm": gemm, "solve": solve, "bytes": byts}
 
 
 def ramp_layers(n: int, chi: int) -> int:
@@ -273,7 +319,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default=None, choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default=None, choices=["fp32", "fp64", "mixed"])
+    ap.add_argument("--centre-only", action="store_true", help="record S at the centre bond only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workers", type=int, default=8, help="host worker threads of the batching form")
     args = ap.parse_args()
@@ -314,7 +361,7 @@ def main():
     hp = [torch.from_numpy(pp.copy()).pin_memory() for pp in circ.p]
 
     stream = torch.cuda.current_stream(dev)
-    m = mpo.MPO(n, chi, prec, stream=stream.cuda_stream)
+    m = mpo.MPO(n, chi, prec, stream=stream.cuda_stream, centre_only=args.centre_only)
     t = 0
 
     def layer_dev(tt):
@@ -385,26 +432,57 @@ def main():
     e2e_value = gates_e2e * world / (e2e_ms / 1e3)
     S, tr, dw = m.entropy()
 
-    # ---- roofline of the dominant kernel class --------------------------------
+    # ---- rooflines -----------------------------------------------------------
+    # (1) the dominant kernel class: its algorithmic flops (or bytes) per
+    # launch as the library counts them, over its CUDA-event time on the
+    # engine's stream, against the peak of the unit it runs on; (2) the whole
+    # step: T_roof = F_gemm / P_gemm + F_solve / P_solve + bytes / BW over the
+    # measured step time.
+    peaks = load_peaks()
     classes = {k: v for k, v in prof.items() if not k.startswith("_") and v["launches"] > 0}
     dom = max(classes, key=lambda k: classes[k]["ms"])
     d = classes[dom]
-    achieved = d["flops"] / (d["ms"] / 1e3)
-    peak = ALU_PEAK[prec]
-    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved / 1e12, "peak": peak / 1e12,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "share_of_step": d["ms"] / ms, "launches": d["launches"],
-                "avg_launch_ms": d["ms"] / d["launches"],
-                "peak_basis": ("FP32 SIMT: 152 SMs x 128 lanes x 2 flop x 2.07 GHz" if prec == "fp32"
-                               else "FP64 nominal 1.25 TFLOP/s")}
-    kernels = {k: {"ms": round(v["ms"], 3), "launches": v["launches"], "share": round(v["ms"] / ms, 4)}
+    fp64_classes = {"refine_gemm", "eig_fp64"} | ({"svd_gate", "svd_sweep", "cgemm"} if prec != "fp32" else set())
+    if prec == "mixed":
+        fp64_classes -= {"svd_gate", "svd_sweep"}      # the FP32 Jacobi SVD of the precision form
+    tensor_classes = {"svd_gate", "svd_sweep", "cgemm", "tc_cgemm"} - fp64_classes
+    if dom in fp64_classes:
+        bound, pk, unit, basis = "alu", peaks["fp64_tflops"], "TFLOP/s", "FP64 FMA probe 1.20 TFLOP/s"
+        achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
+    elif dom in tensor_classes:
+        bound, pk, unit = "tensor", peaks["tf32_tflops"], "TFLOP/s"
+        basis = f"TF32 tensor = BF16 sustained / 2 ({peaks['source']})"
+        achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
+    else:
+        bound, pk, unit, basis = "hbm", peaks["hbm_gbs"], "GB/s", f"HBM copy ({peaks['source']})"
+        achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
+    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": pk, "unit": unit,
+                "frac": achieved / pk, "traffic": None, "peak_basis": basis,
+                "share_of_step": d["ms"] / ms, "launches": d["launches"], "avg_launch_ms": d["ms"] / d["launches"]}
+    over = chi if prec == "mixed" else 0
+    w = {"gemm": 0.0, "solve": 0.0, "bytes": 0.0}
+    for tt in range(t - 2 * K + 1, t - K + 1):          # the timed steps
+        sw = step_work(dims, n, circ.parity(tt), chi, prec, over, args.centre_only)
+        for key in w:
+            w[key] += sw[key]
+    p_gemm = peaks["fp64_tflops"] if prec == "fp64" else peaks["tf32_tflops"]
+    p_solve = peaks["fp32_simt_tflops"] if prec == "fp32" else peaks["fp64_tflops"]
+    t_roof = w["gemm"] / (p_gemm * 1e12) + w["solve"] / (p_solve * 1e12) + w["bytes"] / (peaks["hbm_gbs"] * 1e9)
+    step_roofline = {"t_roof_ms_per_step": 1e3 * t_roof / K, "measured_ms_per_step": ms / K,
+                     "frac": t_roof / (ms / 1e3), "gemm_flops_per_step": w["gemm"] / K,
+                     "solve_flops_per_step": w["solve"] / K, "bytes_per_step": w["bytes"] / K,
+                     "p_gemm_tflops": p_gemm, "p_solve_tflops": p_solve, "hbm_gbs": peaks["hbm_gbs"],
+                     "peaks": peaks["source"]}
+    kernels = {k: {"ms": round(v["ms"], 3), "launches": v["launches"], "share": round(v["ms"] / ms, 4),
+                   "flops": v["flops"], "bytes": v["bytes"]}
                for k, v in classes.items()}
 
     line = {"metric": METRIC, "value": value, "unit": "gates/s", "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+            "dtype": {"fp32": "f32", "fp64": "f64", "mixed": "f32+f64"}[prec], "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "chi_max": chi, "p": p, "seed": wl["seed"],
-                       "precision": prec, "parallelism": f"replicas{world}", "ramp_layers": R,
+                       "precision": prec, "entropy": "centre bond" if args.centre_only else "every bond",
+                       "oversample": over, "parallelism": f"replicas{world}", "ramp_layers": R,
                        "ramp_seconds": round(t_ramp, 2), "gates_per_step": gates_timed / K,
                        "max_bond_dim": int(max(dims)), "l2": "inputs larger than L2 (site tensors "
                        f"{m.device_bytes() / 2**30:.1f} GiB)", "final_S_centre": float(S[n // 2 - 1]),
@@ -412,6 +490,7 @@ def main():
             "clocks": clk,
             "gpu_launches": int(sum(v["launches"] for v in classes.values())),
             "roofline": roofline,
+            "step_roofline": step_roofline,
             "kernels": kernels,
             "svd_sweeps_per_launch": prof["_sweeps"] / max(1, sum(prof.get(k, {}).get("launches", 0)
                                                                     for k in ("svd_gate", "svd_sweep"))),

@@ -54,12 +54,13 @@ typedef struct mpo_ctx *mpo_handle;
  *                   SVD (App. A) and centre move starts from the FP32 one-sided
  *                   Jacobi SVD of an FP32 copy, whose m = chi_max + oversample
  *                   leading left singular vectors are refined in FP64 by
- *                   refine_steps Rayleigh-Ritz-accelerated subspace-iteration
- *                   steps and a final Rayleigh-Ritz projection with an FP64
- *                   Hermitian eigen-solve of the m x m projected Gram; the
- *                   singular values, their normalisation and the entropy are
- *                   FP64. Matches the FP64 form to |dS| <= 1e-6 and a kept-theta
- *                   relative Frobenius error <= 1e-7 per gate. */
+ *                   refine_steps FP64 subspace-iteration steps (shifted
+ *                   CholeskyQR3 orthonormalisation) and a final Rayleigh-Ritz
+ *                   projection B = Q^H theta' whose m x c SVD is an FP64
+ *                   one-sided Jacobi; the singular values, their normalisation
+ *                   and the entropy are FP64. Matches the FP64 form to
+ *                   |dS| <= 1e-6 and a kept-theta relative Frobenius error
+ *                   <= 1e-7 per gate. */
 typedef enum { MPO_FP64 = 0, MPO_FP32 = 1, MPO_MIXED_FP32 = 2 } mpo_precision;
 
 /* Which bonds mpo_entropy reports.
@@ -82,9 +83,8 @@ typedef struct {
   int eig_max_sweeps;       /* cap on Jacobi sweeps per SVD [40, at most 64]; reaching it -> MPO_ERR_NOCONV */
   double sv_rel_cutoff;     /* drop Schmidt values lambda <= cutoff * lambda_max at every
                                factorisation [1e-12 for FP64, 1e-6 for FP32: the rounding
-                               floor of the one-sided Jacobi SVD; 1e-7 for MPO_MIXED_FP32:
-                               the floor of its FP64 Gram eigen-solve]; <= 0 selects the
-                               default */
+                               floor of the one-sided Jacobi SVD; 1e-7 for MPO_MIXED_FP32]; <= 0
+                               selects the default */
   size_t arena_cap_bytes;   /* refuse device allocations above this total [0 = no cap] */
   mpo_entropy_mode smode;   /* [MPO_S_ALL_BONDS] */
   double barrier_timeout_s; /* limit of each device-side grid-barrier wait [5.0] */
@@ -98,10 +98,11 @@ typedef struct {
                                moves) on the tcgen05 tensor cores with 3 x TF32 split products
                                [0 = off: the SIMT FP32 kernel, currently the faster one] */
   int oversample;           /* MPO_MIXED_FP32: extra FP32 singular vectors carried into the FP64
-                               refinement of a truncating SVD, beyond chi_max [0 = chi_max / 2;
+                               refinement of a truncating SVD, beyond chi_max [0 = chi_max;
                                < 0 = none] */
   int refine_steps;         /* MPO_MIXED_FP32: subspace-iteration steps before the final
-                               Rayleigh-Ritz projection of a truncating SVD [0 = 3; < 0 = none] */
+                               Rayleigh-Ritz projection of a truncating SVD [0 = 5, at most 7;
+                               < 0 = none] */
 } mpo_opts;
 
 /* Fill *o with the defaults. */
@@ -241,14 +242,17 @@ size_t mpo_device_bytes(mpo_handle h);
  * counterpart (it is a measurement aid). */
 int mpo_profile(mpo_handle h, int enable);
 
-/* Totals for kernel class cls (0 .. 8: svd_gate (the truncated SVD of a
+/* Totals for kernel class cls (0 .. 11: svd_gate (the truncated SVD of a
  * gate), svd_sweep (the SVDs of centre moves and Schmidt sweeps), cgemm,
- * superop, select, gather, transpose, trace, tc_cgemm) since the last
- * mpo_profile(h, 1): summed event
- * durations in ms, launch count, and the algorithmic flops and bytes of those
- * launches as the library counts them (an SVD of an r x c matrix counts the
- * Gram-plus-dense-eigensolver work 4 min^2 max + 13.3 min^3, a complex GEMM
- * 8 M N K). Returns MPO_ERR_ARG past the last class. Synchronises the stream. */
+ * superop, select, gather, transpose, trace, tc_cgemm, refine_gemm (the FP64
+ * products of the precision form's refinement), eig_fp64 (its FP64 Hermitian
+ * eigen-solves), convert (its FP32 copies)) since the last mpo_profile(h, 1):
+ * summed event durations in ms, launch count, and the algorithmic flops and
+ * bytes of those launches as the library counts them: an SVD of an r x c
+ * matrix (r <= c) keeping k values counts the Hermitian Gram 4 r^2 c, the
+ * projection 8 k r c and, unless the eigen-solve is a launch of its own
+ * (eig_fp64, 13.3 m^3), 13.3 r^3; a complex GEMM 8 M N K. Returns
+ * MPO_ERR_ARG past the last class. Synchronises the stream. */
 int mpo_profile_read(mpo_handle h, int cls, const char **name, double *ms, long long *launches, double *flops,
                      double *bytes);
 

@@ -5,8 +5,8 @@
 //   Q <- the m leading columns of the FP32 left factor, promoted to FP64 and
 //        made orthonormal by Newton-Schulz steps Q <- Q (3 I - Q^H Q) / 2;
 //   subspace iteration Q <- orth(A A^H Q), orth = shifted CholeskyQR3;
-//   Rayleigh-Ritz: B = Q^H A, B B^H = V diag(w) V^H (FP64 Jacobi eigen-solve),
-//        left factor Q V, rows V^H B = Lambda W^H.
+//   Rayleigh-Ritz: B = Q^H A, FP64 one-sided Jacobi SVD B = U_B Lambda W^H,
+//        left factor Q U_B, rows Lambda W^H.
 //
 // The products are the engine's complex GEMM; these kernels convert, gather,
 // form the Newton-Schulz multiplier, factor the diagonal blocks of the
@@ -161,4 +161,10 @@ __global__ void __launch_bounds__(1024) frob2_kernel(const double2* __restrict__
     for (int i = 0; i < (blockDim.x + 31) / 32; ++i) v += red[i];
     *out = v;
   }
+}
+
+// x <- conj(x) for n complex128 entries.
+__global__ void conj_inplace_kernel(double2* __restrict__ x, size_t n) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    x[e].y = -x[e].y;
 }

@@ -121,9 +121,9 @@ struct mpo_ctx {
   double* mx_lam32 = nullptr;
   SelectInfo* mx_info32 = nullptr;
   double2 *mx_Q = nullptr, *mx_Q2 = nullptr, *mx_B = nullptr, *mx_T = nullptr;
-  double2 *mx_H = nullptr, *mx_V = nullptr, *mx_G = nullptr;
+  double2 *mx_V = nullptr, *mx_G = nullptr;
   double* mx_w = nullptr;
-  GridCtl* mx_ctl = nullptr;       // one control block per FP64 eigen-solve of a factorisation
+  OSCtl* mx_osctl = nullptr;       // control block of the FP64 Rayleigh-Ritz SVD
   double2 *mx_linv = nullptr, *mx_ptmp = nullptr;   // Cholesky: diagonal-block inverses, panel scratch
   int* mx_chst = nullptr;          // set when a Cholesky pivot was not positive
   struct MxSync { GridCtl g32; GridCtl eig[8]; };
@@ -339,13 +339,14 @@ static cudaError_t launch_block_jacobi(cudaStream_t st, cplx<T>* X, int r, int c
 //      orth is shifted Cholesky QR followed by two Cholesky QR passes
 //      (shifted CholeskyQR3, stable for condition numbers up to 1/eps).
 //      With m = r the span of Q is the whole row space already.
-//   4. Rayleigh-Ritz: B = Q^H X, H = B B^H = V diag(w) V^H (FP64 Jacobi
-//      eigen-solve). The Ritz values w are the squared singular values, Q V
-//      the left singular vectors and V^H B = Lambda W^H the scaled right ones.
+//   4. Rayleigh-Ritz: B = Q^H X and its FP64 one-sided Jacobi SVD
+//      B = U_B Lambda W^H. The Ritz values w = Lambda^2 are the squared
+//      singular values, Q U_B the left singular vectors and Lambda W^H the
+//      scaled right ones.
 // Outputs follow the one-sided Jacobi convention of svd_select: rows 0..m-1
-// of X are overwritten with V^H B, h->vecs holds V^H Q^H (m x r, row j =
-// conj of left singular vector j: h->vecs_conj), h->mx_w the w; the select
-// kernel then sorts and truncates.
+// of X are overwritten with Lambda W^H, h->vecs holds U_B^H Q^H (m x r, row
+// j = conj of left singular vector j: h->vecs_conj), h->mx_w the w; the
+// select kernel then sorts and truncates.
 // ---------------------------------------------------------------------------
 static cudaError_t mx_gemm(mpo_ctx* h, int M, int N, int K, const double2* A, int lda, int opA, const double2* B,
                            int ldb, int opB, double2* C, int ldc, double alpha = 1.0, int accumulate = 0) {
@@ -435,14 +436,15 @@ static int mx_scholqr3(mpo_ctx* h, double2* Y, int r, int m) {
   return rc;
 }
 
-// B = Q^H X (m x c), H = B B^H, FP64 eigen-solve H = V diag(w) V^H using
-// control block slot `slot`.
+// Rayleigh-Ritz in FP64: B = Q^H X (m x c), then the FP64 one-sided (row)
+// Jacobi SVD of B, B = U_B B' with the rows of B' = Lambda W^H mutually
+// orthogonal; squared row norms -> h->mx_w, U_B^T -> h->mx_V. Working on B
+// itself (not on B B^H) keeps the singular values' relative accuracy.
 static int mx_ritz(mpo_ctx* h, const double2* X, int r, int c, int ldx, int m, int slot) {
   CK(h, mx_gemm(h, m, c, r, h->mx_Q, m, 1, X, ldx, 0, h->mx_B, c));
-  CK(h, mx_gemm(h, m, m, c, h->mx_B, c, 0, h->mx_B, c, 1, h->mx_H, m));
-  ProfScope ps(h, PK_EIG64, 13.3 * (double)m * m * m, 2.0 * m * m * sizeof(double2));
-  CK(h, launch_jacobi<double>(h->st, h->mx_H, m, h->mx_V, h->mx_w, h->mx_ctl + slot, h->opts.eig_max_sweeps,
-                              h->opts.barrier_timeout_s, h->num_sms));
+  ProfScope ps(h, PK_EIG64, 13.3 * (double)m * m * m, (2.0 * m * c + (double)m * m) * sizeof(double2));
+  CK(h, launch_onesided<double>(h->st, h->mx_B, m, c, c, h->mx_V, h->mx_w, h->mx_osctl + slot,
+                                h->opts.eig_max_sweeps, h->opts.barrier_timeout_s, h->num_sms));
   return MPO_OK;
 }
 
@@ -460,8 +462,11 @@ static int msvd_select(mpo_ctx* h, double2* X, int r, int c, int ldx, int cap, b
     CK(h, cudaGetLastError());
   }
   {
-    const double mn = r, mx = c;
-    ProfScope ps(h, disc ? PK_SVD : PK_SVD_SWEEP, 4.0 * mn * mn * mx + 13.3 * mn * mn * mn,
+    // algorithmic work of the approximate SVD: the Hermitian Gram of the short
+    // side (4 r^2 c) and the projection onto the kept vectors (8 k r c); the
+    // FP64 eigen-solve is counted under eig_fp64
+    const double mn = r, mx = c, kk = std::min(cap, r);
+    ProfScope ps(h, disc ? PK_SVD : PK_SVD_SWEEP, 4.0 * mn * mn * mx + 8.0 * kk * mn * mx,
                  (2.0 * r * c + (double)r * r) * sizeof(float2));
     if (h->block_min_rows > 0 && r >= h->block_min_rows)
       CK(h, launch_block_jacobi<float>(h->st, h->mx_a32, r, c, c, h->mx_ut32, h->mx_w32, (float2*)h->bj_gpart,
@@ -495,8 +500,16 @@ static int msvd_select(mpo_ctx* h, double2* X, int r, int c, int ldx, int cap, b
   // 4. Rayleigh-Ritz projection and the outputs in the one-sided Jacobi convention
   rc = mx_ritz(h, X, r, c, ldx, m, 0);
   if (rc) return rc;
-  CK(h, mx_gemm(h, m, r, m, h->mx_V, m, 1, h->mx_Q, m, 1, (double2*)h->vecs, r));   // V^H Q^H
-  CK(h, mx_gemm(h, m, c, m, h->mx_V, m, 1, h->mx_B, c, 0, X, ldx));                   // V^H B
+  // left factor Q U_B, stored as rows conj(column j) = U_B^H Q^H with
+  // U_B^H = conj(U_B^T); the rows Lambda W^H of B' go to X
+  {
+    ProfScope ps(h, PK_REFINE, 0.0, 2.0 * m * m * sizeof(double2));
+    conj_inplace_kernel<<<grid_for((size_t)m * m, h->num_sms), 256, 0, h->st>>>(h->mx_V, (size_t)m * m);
+    CK(h, cudaGetLastError());
+  }
+  CK(h, mx_gemm(h, m, r, m, h->mx_V, m, 0, h->mx_Q, m, 1, (double2*)h->vecs, r));
+  CK(h, cudaMemcpy2DAsync(X, (size_t)ldx * sizeof(double2), h->mx_B, (size_t)c * sizeof(double2),
+                          (size_t)c * sizeof(double2), m, cudaMemcpyDeviceToDevice, h->st));
   h->vecs_conj = true;
   {
     ProfScope ps(h, PK_SELECT, 0.0, (double)m * (sizeof(double) + sizeof(int) + sizeof(double)));
@@ -505,7 +518,7 @@ static int msvd_select(mpo_ctx* h, double2* X, int r, int c, int ldx, int cap, b
   }
   CK(h, cudaMemcpyAsync(&h->hs->info, h->info, sizeof(SelectInfo), cudaMemcpyDeviceToHost, h->st));
   CK(h, cudaMemcpyAsync(&h->hs->ctl, &h->osctl->g, sizeof(GridCtl), cudaMemcpyDeviceToHost, h->st));
-  CK(h, cudaMemcpyAsync(h->hs->eig, h->mx_ctl, sizeof(GridCtl), cudaMemcpyDeviceToHost, h->st));
+  CK(h, cudaMemcpyAsync(h->hs->eig, &h->mx_osctl->g, sizeof(GridCtl), cudaMemcpyDeviceToHost, h->st));
   CK(h, cudaMemcpyAsync(&h->hs->chol_status, h->mx_chst, sizeof(int), cudaMemcpyDeviceToHost, h->st));
   if (h->prof) CK(h, cudaMemcpyAsync(h->hs->phase_ns, h->osctl->phase_ns, sizeof(h->hs->phase_ns), cudaMemcpyDeviceToHost, h->st));
   CK(h, cudaStreamSynchronize(h->st));
@@ -515,11 +528,11 @@ static int msvd_select(mpo_ctx* h, double2* X, int r, int c, int ldx, int cap, b
   h->prof_sweeps += h->prof ? h->hs->ctl.sweeps : 0;
   if (h->hs->ctl.status)
     return fail(h, MPO_ERR_NOCONV, "FP32 Jacobi SVD reached eig_max_sweeps (" + std::to_string(r) + " x " + std::to_string(c) + ")");
-  if (h->hs->eig[0].err) return fail(h, MPO_ERR_TIMEOUT, "grid barrier wait timed out in the FP64 eigen-solve");
-  if (h->hs->eig[0].status)
-    return fail(h, MPO_ERR_NOCONV, "FP64 eigen-solve reached eig_max_sweeps (m = " + std::to_string(m) + ")");
   if (h->hs->chol_status)
     return fail(h, MPO_ERR_NOCONV, "Cholesky QR met a non-positive pivot (m = " + std::to_string(m) + ")");
+  if (h->hs->eig[0].err) return fail(h, MPO_ERR_TIMEOUT, "grid barrier wait timed out in the FP64 Rayleigh-Ritz SVD");
+  if (h->hs->eig[0].status)
+    return fail(h, MPO_ERR_NOCONV, "FP64 Rayleigh-Ritz SVD reached eig_max_sweeps (m = " + std::to_string(m) + ")");
   *k = h->hs->info.k;
   return MPO_OK;
 }
@@ -536,10 +549,11 @@ static int svd_select(mpo_ctx* h, cplx<T>* X, int r, int c, int ldx, int cap, bo
   T* w = (T*)h->wv;
   {
     // algorithmic work of the factorisation: Hermitian Gram of the short side
-    // (4 mn^2 mx real flops) plus its dense eigen-decomposition (13.3 mn^3);
-    // bytes: read and write X, write U
-    const double mn = std::min(r, c), mx = std::max(r, c);
-    ProfScope ps(h, disc ? PK_SVD : PK_SVD_SWEEP, 4.0 * mn * mn * mx + 13.3 * mn * mn * mn,
+    // (4 mn^2 mx real flops), projection onto the kept vectors (8 k mn mx) and
+    // the dense Hermitian eigen-decomposition (13.3 mn^3); bytes: read and
+    // write X, write U
+    const double mn = std::min(r, c), mx = std::max(r, c), kk = std::min(cap, (int)mn);
+    ProfScope ps(h, disc ? PK_SVD : PK_SVD_SWEEP, 4.0 * mn * mn * mx + 8.0 * kk * mn * mx + 13.3 * mn * mn * mn,
                  (2.0 * r * c + (double)r * r) * sizeof(cplx<T>));
     if (h->block_min_rows > 0 && r >= h->block_min_rows)
       CK(h, launch_block_jacobi<T>(h->st, X, r, c, ldx, (cplx<T>*)h->vecs, w, (cplx<T>*)h->bj_gpart, h->bj_slots,
@@ -940,11 +954,10 @@ static bool alloc_factor_ws(mpo_ctx* h, int m, int ccap, size_t bj_nch) {
     ok = ok && alloc((void**)&h->mx_Q2, (size_t)m * mm * sizeof(double2));
     ok = ok && alloc((void**)&h->mx_B, (size_t)ccap * mm * sizeof(double2));
     ok = ok && alloc((void**)&h->mx_T, (size_t)ccap * mm * sizeof(double2));
-    ok = ok && alloc((void**)&h->mx_H, mm * mm * sizeof(double2));
     ok = ok && alloc((void**)&h->mx_V, mm * mm * sizeof(double2));
     ok = ok && alloc((void**)&h->mx_G, mm * mm * sizeof(double2));
     ok = ok && alloc((void**)&h->mx_w, mm * sizeof(double));
-    ok = ok && alloc((void**)&h->mx_ctl, 8 * sizeof(GridCtl));
+    ok = ok && alloc((void**)&h->mx_osctl, sizeof(OSCtl));
     ok = ok && alloc((void**)&h->mx_linv, (mm / CHOL_NB + 1) * CHOL_NB * CHOL_NB * sizeof(double2));
     ok = ok && alloc((void**)&h->mx_ptmp, (size_t)std::max<size_t>(m, mm) * CHOL_NB * sizeof(double2));
     ok = ok && alloc((void**)&h->mx_chst, sizeof(int));
@@ -1021,7 +1034,7 @@ int mpo_init(mpo_handle* out, int n, int chi_max, mpo_precision prec, void* stre
                                       (size_t)m * (sizeof(float) + sizeof(int) + sizeof(double)) +
                                       2 * (size_t)m * h->mx_mcap * sizeof(double2) +
                                       2 * (size_t)mx_ccap * h->mx_mcap * sizeof(double2) +
-                                      4 * (size_t)h->mx_mcap * h->mx_mcap * sizeof(double2) +
+                                      2 * (size_t)h->mx_mcap * h->mx_mcap * sizeof(double2) +
                                       (size_t)std::max(m, h->mx_mcap) * CHOL_NB * sizeof(double2) +
                                       (size_t)h->mx_mcap * sizeof(double)
                                 : 0);
@@ -1091,7 +1104,7 @@ void mpo_free(mpo_handle h) {
   void* ps[] = {h->spare, h->theta, h->theta2, h->osctl, h->tc_status, h->bj_gpart, h->bj_j, h->bj_act, h->vecs, h->tmp, h->wv, h->perm, h->lam2, h->Ms, h->dgates,
                 h->dsup, h->dp, h->info, h->ctl, h->scal, h->dS, h->dschmidt, h->tv0, h->tv1,
                 h->mx_a32, h->mx_ut32, h->mx_w32, h->mx_perm32, h->mx_lam32, h->mx_info32, h->mx_Q, h->mx_Q2,
-                h->mx_B, h->mx_T, h->mx_H, h->mx_V, h->mx_G, h->mx_w, h->mx_ctl,
+                h->mx_B, h->mx_T, h->mx_V, h->mx_G, h->mx_w, h->mx_osctl,
                 h->mx_linv, h->mx_ptmp, h->mx_chst};
   for (void* p : ps) if (p) cudaFree(p);
   if (h->hs) cudaFreeHost(h->hs);
