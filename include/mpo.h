@@ -94,9 +94,12 @@ typedef struct {
                                < 0 = never]. The block form needs far fewer passes over
                                the matrix but resolves singular values only to about
                                sqrt(eps) * sigma_max relative accuracy per row pair. */
-  int tensor_cores;         /* FP32 only: > 0 runs the plain complex products (theta, centre
+  int tensor_cores;         /* MPO_FP32: > 0 runs the plain complex products (theta, centre
                                moves) on the tcgen05 tensor cores with 3 x TF32 split products
-                               [0 = off: the SIMT FP32 kernel, currently the faster one] */
+                               [0 = off: the SIMT FP32 kernel, currently the faster one].
+                               MPO_MIXED_FP32: >= 0 runs its FP64 products (theta, the
+                               refinement and the projections) on the tensor cores as
+                               FP64-accurate BF16 split products [0 = on; < 0 = SIMT FP64] */
   int oversample;           /* MPO_MIXED_FP32: extra FP32 singular vectors carried into the FP64
                                refinement of a truncating SVD, beyond chi_max [0 = chi_max;
                                < 0 = none] */
@@ -350,6 +353,19 @@ int mpo_svd_static(int r, int c, void *X, void *w, void *Ut, mpo_precision prec,
  * split products, 0 the SIMT kernel of the given precision. */
 int mpo_gemm(int M, int N, int K, const void *A, const void *B, void *C, mpo_precision prec, int tensor_cores,
              void *cuda_stream);
+
+/* The same product with explicit operand forms and engines, exported for
+ * tests: C (M x N, leading dimension ldc) = op(A) op(B), op 0 = as stored,
+ * op 1 = conjugate transpose (A is then stored K x M with leading dimension
+ * lda, B N x K with ldb), device pointers. engine 0 runs the SIMT kernel of
+ * the given precision; engine 1 the tensor cores: for MPO_FP32 the 3 x TF32
+ * kernel (opA = opB = 0 only, as mpo_gemm), for MPO_FP64 the FP64-accurate
+ * product from BF16 slices with FP32 accumulation that the precision form
+ * uses (each operand split into 6 slices of 7 bits under a power-of-two
+ * scale per row / column; relative error about 2^-42 of |row| |column|).
+ * Allocates its scratch per call and waits for the stream. */
+int mpo_gemm_ex(int M, int N, int K, const void *A, int lda, int opA, const void *B, int ldb, int opB, void *C,
+                int ldc, mpo_precision prec, int engine, void *cuda_stream);
 
 /* Library version string. */
 const char *mpo_version(void);

@@ -44,6 +44,7 @@
 #include "mpo_kernels.cuh"
 #include "mixed.cuh"
 #include "tcgemm.cuh"
+#include "ozgemm.cuh"
 
 namespace {
 
@@ -58,11 +59,22 @@ struct HostSync {   // pinned read-back of the last select + eigen-solve
   int tc_err;
   GridCtl eig[8];     // FP64 eigen-solves of the last mixed factorisation
   int chol_status;    // Cholesky QR pivot status of the last mixed factorisation
+  int oz_err;         // the tensor-core FP64 GEMM's wait-limit flag
 };
 
 }  // namespace
 
 struct BatchState;
+
+// Scratch of the FP64-accurate tensor-core GEMM: the BF16 slices of both
+// operands and their row / column exponents (sized for the largest product
+// the handle issues).
+struct OzWork {
+  __nv_bfloat16 *a = nullptr, *b = nullptr;
+  int *ea = nullptr, *eb = nullptr, *status = nullptr;
+  size_t a_cap = 0, b_cap = 0;     // elements
+  int e_cap = 0;
+};
 
 struct mpo_ctx {
   BatchState* batch = nullptr;     // set on handles made by mpo_init_batch
@@ -126,6 +138,8 @@ struct mpo_ctx {
   OSCtl* mx_osctl = nullptr;       // control block of the FP64 Rayleigh-Ritz SVD
   double2 *mx_linv = nullptr, *mx_ptmp = nullptr;   // Cholesky: diagonal-block inverses, panel scratch
   int* mx_chst = nullptr;          // set when a Cholesky pivot was not positive
+  OzWork oz;                       // FP64-accurate tensor-core GEMM scratch (precision form)
+  bool use_oz = false;
   struct MxSync { GridCtl g32; GridCtl eig[8]; };
   bool prof = false;
   struct Pending { int cls; cudaEvent_t a, b; double flops, bytes; };
@@ -138,9 +152,9 @@ struct mpo_ctx {
 };
 
 enum { PK_SVD = 0, PK_SVD_SWEEP, PK_GEMM, PK_SUPEROP, PK_SELECT, PK_GATHER, PK_TRANSPOSE, PK_TRACE, PK_TCGEMM,
-       PK_REFINE, PK_EIG64, PK_CONVERT, PK_NCLASS };
+       PK_REFINE, PK_EIG64, PK_CONVERT, PK_OZ, PK_NCLASS };
 static const char* kProfNames[PK_NCLASS] = {"svd_gate", "svd_sweep", "cgemm", "superop", "select", "gather", "transpose", "trace",
-                                            "tc_cgemm", "refine_gemm", "eig_fp64", "convert"};
+                                            "tc_cgemm", "refine_gemm", "eig_fp64", "convert", "oz_gemm"};
 
 static cudaEvent_t prof_event(mpo_ctx* h) {
   if (!h->evpool.empty()) { cudaEvent_t e = h->evpool.back(); h->evpool.pop_back(); return e; }
@@ -334,10 +348,12 @@ static cudaError_t launch_block_jacobi(cudaStream_t st, cplx<T>* X, int r, int c
 //   2. Q (r x m, FP64) = the m = min(r, cap + oversample) leading columns of U,
 //      made orthonormal to FP64 rounding by Newton-Schulz steps.
 //   3. If m < r (the truncation can bite), refine_steps subspace-iteration
-//      steps Q <- orth(X X^H Q) in FP64, each damping the components of the
-//      leading singular vectors outside span(Q) by (sigma_{m+1} / sigma_j)^2;
-//      orth is shifted Cholesky QR followed by two Cholesky QR passes
-//      (shifted CholeskyQR3, stable for condition numbers up to 1/eps).
+//      steps W <- orth(X^H Q), Q <- orth(X W) in FP64, each damping the
+//      components of the leading singular vectors outside span(Q) by
+//      (sigma_{m+1} / sigma_j)^2; orth is shifted Cholesky QR followed by two
+//      Cholesky QR passes (shifted CholeskyQR3, stable for condition numbers
+//      up to 1/u), applied after each product so that a basis never carries
+//      more than the condition number sigma_1 / sigma_m.
 //      With m = r the span of Q is the whole row space already.
 //   4. Rayleigh-Ritz: B = Q^H X and its FP64 one-sided Jacobi SVD
 //      B = U_B Lambda W^H. The Ritz values w = Lambda^2 are the squared
@@ -348,9 +364,69 @@ static cudaError_t launch_block_jacobi(cudaStream_t st, cplx<T>* X, int r, int c
 // j = conj of left singular vector j: h->vecs_conj), h->mx_w the w; the
 // select kernel then sorts and truncates.
 // ---------------------------------------------------------------------------
+// C (M x N) = alpha op(A) op(B) (+ C), complex128, FP64-accurate on the
+// tensor cores (ozgemm.cuh): exponents, BF16 slices of both operands, then
+// the MMA kernel. Returns cudaErrorInvalidValue if the scratch is too small.
+static cudaError_t oz_gemm(cudaStream_t st, int M, int N, int K, const double2* A, int lda, int opA, const double2* B,
+                           int ldb, int opB, double2* C, int ldc, double alpha, int accumulate, const OzWork& w,
+                           double timeout_s, int num_sms) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  const int K8 = (std::max(K, 1) + 31) / 32 * 32;
+  const int Mp = (M + oz::BM - 1) / oz::BM * oz::BM, Nrp = (2 * N + oz::BN - 1) / oz::BN * oz::BN;
+  const size_t Kp = 2 * (size_t)K8;
+  if ((size_t)oz::S * Mp * Kp > w.a_cap || (size_t)oz::S * Nrp * Kp > w.b_cap || Mp > w.e_cap || Nrp / 2 > w.e_cap)
+    return cudaErrorInvalidValue;
+  const int g = std::max(1, std::min(num_sms * 8, (std::max(M, N) + 255) / 256 * 8));
+  oz_row_exp_kernel<<<g, 256, 0, st>>>(A, lda, opA, M, K, w.ea);
+  oz_col_exp_kernel<<<g, 256, 0, st>>>(B, ldb, opB, K, N, w.eb);
+  oz_split_a_kernel<<<dim3(K8 / 32, Mp / 32), dim3(32, 8), 0, st>>>(A, lda, opA, M, K, K8, Mp, w.ea, w.a);
+  oz_split_b_kernel<<<dim3(K8 / 32, Nrp / 64), dim3(32, 8), 0, st>>>(B, ldb, opB, K, N, K8, Nrp, w.eb, w.b);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = ensure_dynamic_smem((const void*)oz_mma_kernel, oz::SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  oz_mma_kernel<<<dim3(Nrp / oz::BN, Mp / oz::BM), oz::NT, oz::SMEM_BYTES, st>>>(
+      M, N, (int)Kp, w.a, (size_t)Mp * Kp, w.b, (size_t)Nrp * Kp, w.ea, w.eb, C, ldc, alpha, accumulate, w.status,
+      (long long)(timeout_s * 1e9));
+  return cudaGetLastError();
+}
+
+// Allocate the scratch for products whose operands have at most dmax rows,
+// columns and inner dimension.
+static bool alloc_oz(OzWork& w, int dmax, size_t* bytes) {
+  const size_t Mp = (size_t)(dmax + oz::BM - 1) / oz::BM * oz::BM;
+  const size_t Nrp = (size_t)(2 * dmax + oz::BN - 1) / oz::BN * oz::BN;
+  const size_t Kp = 2 * (size_t)((dmax + 31) / 32 * 32);
+  w.a_cap = (size_t)oz::S * Mp * Kp;
+  w.b_cap = (size_t)oz::S * Nrp * Kp;
+  w.e_cap = (int)std::max(Mp, Nrp);
+  bool ok = cudaMalloc((void**)&w.a, w.a_cap * sizeof(__nv_bfloat16)) == cudaSuccess &&
+            cudaMalloc((void**)&w.b, w.b_cap * sizeof(__nv_bfloat16)) == cudaSuccess &&
+            cudaMalloc((void**)&w.ea, w.e_cap * sizeof(int)) == cudaSuccess &&
+            cudaMalloc((void**)&w.eb, w.e_cap * sizeof(int)) == cudaSuccess &&
+            cudaMalloc((void**)&w.status, sizeof(int)) == cudaSuccess &&
+            cudaMemset(w.status, 0, sizeof(int)) == cudaSuccess;
+  if (!ok) cudaGetLastError();
+  if (bytes) *bytes += (w.a_cap + w.b_cap) * sizeof(__nv_bfloat16) + 2 * w.e_cap * sizeof(int);
+  return ok;
+}
+
+static void free_oz(OzWork& w) {
+  cudaFree(w.a); cudaFree(w.b); cudaFree(w.ea); cudaFree(w.eb); cudaFree(w.status);
+  w = OzWork();
+}
+
+// Products large enough to fill 128 x 128 real tiles go to the tensor cores.
+static bool oz_worth(int M, int N, int K) { return (double)M * N * K >= 1.6e7 && M >= 32 && N >= 16 && K >= 32; }
+
 static cudaError_t mx_gemm(mpo_ctx* h, int M, int N, int K, const double2* A, int lda, int opA, const double2* B,
                            int ldb, int opB, double2* C, int ldc, double alpha = 1.0, int accumulate = 0) {
   ProfScope ps(h, PK_REFINE, 8.0 * M * N * K, (double)((size_t)M * K + (size_t)K * N + (size_t)M * N) * sizeof(double2));
+  if (h->use_oz && oz_worth(M, N, K)) {
+    ps.cls = PK_OZ;
+    return oz_gemm(h->st, M, N, K, A, lda, opA, B, ldb, opB, C, ldc, alpha, accumulate, h->oz,
+                   h->opts.barrier_timeout_s, h->num_sms);
+  }
   return cgemm<double>(h->st, M, N, K, A, lda, opA, B, ldb, opB, C, ldc, nullptr, alpha, accumulate);
 }
 
@@ -427,9 +503,12 @@ static int mx_cholqr(mpo_ctx* h, double2* Y, int r, int m, double shift_rel) {
 // Shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto & Yanagisawa,
 // SIAM J. Sci. Comput. 2020): one Cholesky QR with the shift
 // 11 (r m + m (m + 1)) u ||Y||^2 makes the basis well conditioned, two plain
-// passes make it orthonormal to rounding.
+// passes make it orthonormal to rounding. u is the unit roundoff of the
+// products: FP64's, or 2^-40 for the tensor-core split products (their
+// error is about 2^-42 of |row| |column|), so that the shift dominates the
+// Gram matrix's own error and every pivot stays positive.
 static int mx_scholqr3(mpo_ctx* h, double2* Y, int r, int m) {
-  const double u = 1.1102230246251565e-16;
+  const double u = h->use_oz ? 9.094947017729282e-13 : 1.1102230246251565e-16;
   int rc = mx_cholqr(h, Y, r, m, 11.0 * ((double)r * m + (double)m * (m + 1)) * u);
   if (!rc) rc = mx_cholqr(h, Y, r, m, 0.0);
   if (!rc) rc = mx_cholqr(h, Y, r, m, 0.0);
@@ -489,9 +568,13 @@ static int msvd_select(mpo_ctx* h, double2* X, int r, int c, int ldx, int cap, b
   }
   int rc = mx_orthonormalise(h, r, m);
   if (rc) return rc;
-  // 3. subspace iteration in FP64: Q <- orth(X X^H Q)
+  // 3. subspace iteration in FP64, orthonormalising after each of the two
+  // products (W <- orth(X^H Q), Q <- orth(X W)), so that each basis has
+  // condition number sigma_1 / sigma_m rather than its square
   for (int it = 0; it < steps; ++it) {
     CK(h, mx_gemm(h, c, m, r, X, ldx, 1, h->mx_Q, m, 0, h->mx_T, m));     // T = X^H Q (c x m)
+    rc = mx_scholqr3(h, h->mx_T, c, m);
+    if (rc) return rc;
     CK(h, mx_gemm(h, r, m, c, X, ldx, 0, h->mx_T, m, 0, h->mx_Q2, m));    // X T (r x m)
     std::swap(h->mx_Q, h->mx_Q2);
     rc = mx_scholqr3(h, h->mx_Q, r, m);
@@ -520,6 +603,7 @@ static int msvd_select(mpo_ctx* h, double2* X, int r, int c, int ldx, int cap, b
   CK(h, cudaMemcpyAsync(&h->hs->ctl, &h->osctl->g, sizeof(GridCtl), cudaMemcpyDeviceToHost, h->st));
   CK(h, cudaMemcpyAsync(h->hs->eig, &h->mx_osctl->g, sizeof(GridCtl), cudaMemcpyDeviceToHost, h->st));
   CK(h, cudaMemcpyAsync(&h->hs->chol_status, h->mx_chst, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  if (h->use_oz) CK(h, cudaMemcpyAsync(&h->hs->oz_err, h->oz.status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
   if (h->prof) CK(h, cudaMemcpyAsync(h->hs->phase_ns, h->osctl->phase_ns, sizeof(h->hs->phase_ns), cudaMemcpyDeviceToHost, h->st));
   CK(h, cudaStreamSynchronize(h->st));
   if (h->prof) for (int i = 0; i < 3; ++i) h->prof_phase_ns[i] += h->hs->phase_ns[i];
@@ -528,6 +612,7 @@ static int msvd_select(mpo_ctx* h, double2* X, int r, int c, int ldx, int cap, b
   h->prof_sweeps += h->prof ? h->hs->ctl.sweeps : 0;
   if (h->hs->ctl.status)
     return fail(h, MPO_ERR_NOCONV, "FP32 Jacobi SVD reached eig_max_sweeps (" + std::to_string(r) + " x " + std::to_string(c) + ")");
+  if (h->use_oz && h->hs->oz_err) return fail(h, MPO_ERR_TIMEOUT, "an mbarrier wait timed out in the tensor-core FP64 GEMM");
   if (h->hs->chol_status)
     return fail(h, MPO_ERR_NOCONV, "Cholesky QR met a non-positive pivot (m = " + std::to_string(m) + ")");
   if (h->hs->eig[0].err) return fail(h, MPO_ERR_TIMEOUT, "grid barrier wait timed out in the FP64 Rayleigh-Ritz SVD");
@@ -607,6 +692,13 @@ template <typename T>
 static cudaError_t gemm_p(mpo_ctx* h, int M, int N, int K, const cplx<T>* A, int lda, int opA, const cplx<T>* B,
                           int ldb, int opB, cplx<T>* C, int ldc, const double* alpha_dev = nullptr) {
   ProfScope ps(h, PK_GEMM, 8.0 * M * N * K, (double)((size_t)M * K + (size_t)K * N + (size_t)M * N) * sizeof(cplx<T>));
+  if constexpr (std::is_same<T, double>::value) {
+    if (h->use_oz && !alpha_dev && oz_worth(M, N, K)) {
+      ps.cls = PK_OZ;
+      return oz_gemm(h->st, M, N, K, A, lda, opA, B, ldb, opB, C, ldc, 1.0, 0, h->oz, h->opts.barrier_timeout_s,
+                     h->num_sms);
+    }
+  }
   if constexpr (std::is_same<T, float>::value) {
     if (h->tensor_cores && opA == 0 && opB == 0 && use_tensor_cores(M, N, K)) {
       ps.cls = PK_TCGEMM;
@@ -959,7 +1051,7 @@ static bool alloc_factor_ws(mpo_ctx* h, int m, int ccap, size_t bj_nch) {
     ok = ok && alloc((void**)&h->mx_w, mm * sizeof(double));
     ok = ok && alloc((void**)&h->mx_osctl, sizeof(OSCtl));
     ok = ok && alloc((void**)&h->mx_linv, (mm / CHOL_NB + 1) * CHOL_NB * CHOL_NB * sizeof(double2));
-    ok = ok && alloc((void**)&h->mx_ptmp, (size_t)std::max<size_t>(m, mm) * CHOL_NB * sizeof(double2));
+    ok = ok && alloc((void**)&h->mx_ptmp, std::max<size_t>(std::max<size_t>(m, ccap), mm) * CHOL_NB * sizeof(double2));
     ok = ok && alloc((void**)&h->mx_chst, sizeof(int));
   }
   return ok;
@@ -1021,6 +1113,8 @@ int mpo_init(mpo_handle* out, int n, int chi_max, mpo_precision prec, void* stre
   h->mx_over = h->opts.oversample > 0 ? h->opts.oversample : (h->opts.oversample < 0 ? 0 : chi_max);
   h->mx_steps = h->opts.refine_steps > 0 ? std::min(h->opts.refine_steps, 7) : (h->opts.refine_steps < 0 ? 0 : 5);
   h->mx_mcap = std::min(m, chi_max + h->mx_over);
+  // FP64-accurate products on the tensor cores (BF16 slices) unless switched off
+  h->use_oz = h->mixed && h->opts.tensor_cores >= 0;
   int mx_ccap = 1;   // longest row of a factorised matrix
   for (int i = 0; i + 1 < n; ++i) mx_ccap = std::max(mx_ccap, 4 * std::max(h->cap[i], h->cap[i + 2]));
   for (int b = 0; b + 1 <= n; ++b) mx_ccap = std::max(mx_ccap, 4 * h->cap[std::min(b + 1, n)]);
@@ -1035,9 +1129,12 @@ int mpo_init(mpo_handle* out, int n, int chi_max, mpo_precision prec, void* stre
                                       2 * (size_t)m * h->mx_mcap * sizeof(double2) +
                                       2 * (size_t)mx_ccap * h->mx_mcap * sizeof(double2) +
                                       2 * (size_t)h->mx_mcap * h->mx_mcap * sizeof(double2) +
-                                      (size_t)std::max(m, h->mx_mcap) * CHOL_NB * sizeof(double2) +
+                                      (size_t)std::max(std::max(m, mx_ccap), h->mx_mcap) * CHOL_NB * sizeof(double2) +
                                       (size_t)h->mx_mcap * sizeof(double)
-                                : 0);
+                                : 0) +
+                      (h->use_oz ? (size_t)oz::S * 2 * 3 * (size_t)std::max(m, mx_ccap) * 2 *
+                                       (size_t)((std::max(m, mx_ccap) + 127) / 128 * 128)
+                                 : 0);
   if (h->opts.arena_cap_bytes > 0 && need > h->opts.arena_cap_bytes)
     return init_fail(h, MPO_ERR_OOM, "device memory needed (" + std::to_string(need) + " B) exceeds arena_cap_bytes");
   size_t freeb = 0, totb = 0;
@@ -1057,6 +1154,7 @@ int mpo_init(mpo_handle* out, int n, int chi_max, mpo_precision prec, void* stre
   ok = ok && alloc((void**)&h->dp, (size_t)std::max(1, ngmax) * sizeof(double));
   ok = ok && alloc((void**)&h->dsup, 256 * sizeof(double2));
   ok = ok && alloc_factor_ws(h, m, mx_ccap, bj_nch);
+  if (ok && h->use_oz) ok = alloc_oz(h->oz, std::max(m, mx_ccap), &h->bytes);
   ok = ok && alloc((void**)&h->scal, 4 * sizeof(double));
   ok = ok && alloc((void**)&h->dS, (size_t)(n - 1) * sizeof(double));
   ok = ok && alloc((void**)&h->dschmidt, (size_t)(n - 1) * chi_max * sizeof(double));
@@ -1108,6 +1206,7 @@ void mpo_free(mpo_handle h) {
                 h->mx_linv, h->mx_ptmp, h->mx_chst};
   for (void* p : ps) if (p) cudaFree(p);
   if (h->hs) cudaFreeHost(h->hs);
+  free_oz(h->oz);
   for (auto& q : h->pend) { cudaEventDestroy(q.a); cudaEventDestroy(q.b); }
   for (auto e : h->evpool) cudaEventDestroy(e);
   delete h;
@@ -1406,9 +1505,11 @@ int mpo_svd_truncated(int r, int c, const void* A, int cap, mpo_precision prec, 
   h->mx_over = h->opts.oversample > 0 ? h->opts.oversample : (h->opts.oversample < 0 ? 0 : cap);
   h->mx_steps = h->opts.refine_steps > 0 ? std::min(h->opts.refine_steps, 7) : (h->opts.refine_steps < 0 ? 0 : 5);
   h->mx_mcap = std::min(r, cap + h->mx_over);
+  h->use_oz = h->mixed && h->opts.tensor_cores >= 0;
   const size_t nch = (size_t)(c + JCW - 1) / JCW + 1;
   bool ok = ws_alloc(h, &h->theta, (size_t)r * c * h->esz) && alloc_factor_ws(h, r, c, nch) &&
             ws_alloc(h, (void**)&h->scal, 4 * sizeof(double));
+  if (ok && h->use_oz) ok = alloc_oz(h->oz, c, &h->bytes);
   if (ok && cudaMallocHost((void**)&h->hs, sizeof(HostSync)) != cudaSuccess) { cudaGetLastError(); h->hs = nullptr; ok = false; }
   if (!ok) { mpo_free(h); g_last_init_error = "mpo_svd_truncated: allocation failed"; return MPO_ERR_OOM; }
   int rc = MPO_OK, kk = 0;
@@ -1545,6 +1646,38 @@ int mpo_gemm(int M, int N, int K, const void* A, const void* B, void* C, mpo_pre
   if (e == cudaSuccess && status) e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (status) cudaFree(status);
+  if (e != cudaSuccess) { g_last_init_error = cudaGetErrorString(e); return MPO_ERR_CUDA; }
+  return hs ? MPO_ERR_TIMEOUT : MPO_OK;
+}
+
+int mpo_gemm_ex(int M, int N, int K, const void* A, int lda, int opA, const void* B, int ldb, int opB, void* C,
+                int ldc, mpo_precision prec, int engine, void* stream) {
+  if (M < 1 || N < 1 || K < 1 || !A || !B || !C || (opA != 0 && opA != 1) || (opB != 0 && opB != 1) ||
+      (prec != MPO_FP64 && prec != MPO_FP32) || (engine != 0 && engine != 1))
+    return MPO_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MPO_ERR_CUDA;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaSuccess;
+  int hs = 0;
+  if (prec == MPO_FP64 && engine == 1) {
+    OzWork w;
+    if (!alloc_oz(w, std::max(M, std::max(N, K)), nullptr)) { free_oz(w); return MPO_ERR_OOM; }
+    e = oz_gemm(st, M, N, K, (const double2*)A, lda, opA, (const double2*)B, ldb, opB, (double2*)C, ldc, 1.0, 0, w,
+                5.0, sms);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, w.status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    free_oz(w);
+  } else if (engine == 1) {
+    return mpo_gemm(M, N, K, A, B, C, prec, 1, stream);
+  } else {
+    e = prec == MPO_FP64 ? cgemm<double>(st, M, N, K, (const double2*)A, lda, opA, (const double2*)B, ldb, opB,
+                                         (double2*)C, ldc)
+                         : cgemm<float>(st, M, N, K, (const float2*)A, lda, opA, (const float2*)B, ldb, opB,
+                                        (float2*)C, ldc);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
   if (e != cudaSuccess) { g_last_init_error = cudaGetErrorString(e); return MPO_ERR_CUDA; }
   return hs ? MPO_ERR_TIMEOUT : MPO_OK;
 }

@@ -23,7 +23,7 @@ EXPORTS = ["mpo_default_opts", "mpo_init", "mpo_apply_layer", "mpo_apply_gate", 
            "mpo_device_bytes", "mpo_free", "mpo_last_error", "mpo_eigh", "mpo_svd", "mpo_version",
            "mpo_profile", "mpo_profile_read", "mpo_profile_sweeps", "mpo_profile_phases", "mpo_svd_static",
            "mpo_probability", "mpo_sample", "mpo_gemm", "mpo_svd_last_stats",
-           "mpo_init_batch", "mpo_apply_layer_batch", "mpo_batch_instance", "mpo_svd_truncated"]
+           "mpo_init_batch", "mpo_apply_layer_batch", "mpo_batch_instance", "mpo_svd_truncated", "mpo_gemm_ex"]
 
 
 class MPOError(RuntimeError):
@@ -85,6 +85,7 @@ def load_library(path: str | None = None):
         "mpo_apply_layer_batch": (I, [P, I, P, DP, IP, DP, DP, DP]),
         "mpo_batch_instance": (I, [P, I, ctypes.POINTER(P)]),
         "mpo_svd_truncated": (I, [I, I, P, I, I, ctypes.POINTER(Opts), P, P, DP, IP, P]),
+        "mpo_gemm_ex": (I, [I, I, I, P, I, I, P, I, I, P, I, I, I, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -452,3 +453,19 @@ def svd_truncated(A, cap: int, precision: str = "mixed", **opts):
         raise MPOError(rc, lib.mpo_last_error(None).decode())
     kk = k.value
     return U[:, :kk], X[:kk], lam2[:kk]
+
+
+def gemm_ex(A, B, opA: int = 0, opB: int = 0, precision: str = "fp64", engine: int = 1):
+    """C = op(A) op(B) through mpo_gemm_ex (test export); op 1 = conjugate
+    transpose. A, B: contiguous CUDA complex tensors."""
+    import torch
+    lib = load_library()
+    M = A.shape[1] if opA else A.shape[0]
+    K = A.shape[0] if opA else A.shape[1]
+    N = B.shape[0] if opB else B.shape[1]
+    C = torch.zeros((M, N), dtype=A.dtype, device=A.device)
+    rc = lib.mpo_gemm_ex(M, N, K, A.data_ptr(), A.shape[1], opA, B.data_ptr(), B.shape[1], opB, C.data_ptr(), N,
+                         PRECISIONS[precision], engine, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if rc != 0:
+        raise MPOError(rc, lib.mpo_last_error(None).decode())
+    return C

@@ -66,7 +66,8 @@ def check_kept(M, A, cap, precision="mixed", **opts):
     ref, l2ref = lapack_truncation(A, cap, 1e-12)
     got = U @ X
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-    # the left factor is an isometry to FP64 rounding
+    # the left factor is an isometry to the accuracy of the FP64-class
+    # products (tensor-core split products: about 1e-11)
     iso = np.abs(U.conj().T @ U - np.eye(U.shape[1])).max()
     return err, iso, lam2, l2ref
 
@@ -85,7 +86,7 @@ def test_mixed_kept_theta_per_gate(M, n, chi, depth, seed):
         err, iso, lam2, l2ref = check_kept(M, th, chi)
         worst = max(worst, err)
         assert err <= KEPT_TOL, f"kept-theta error {err:.2e} on a {th.shape} gate"
-        assert iso < 1e-12
+        assert iso < 1e-10
         kk = min(len(lam2), len(l2ref))
         # the precision form drops lambda <= 1e-7 lambda_max (its cutoff), the
         # FP64 reference only lambda <= 1e-12 lambda_max
@@ -96,16 +97,17 @@ def test_mixed_kept_theta_per_gate(M, n, chi, depth, seed):
 
 def test_mixed_exact_when_nothing_is_truncated(M):
     """With m = r the refined basis spans the whole row space: the mixed SVD
-    equals the FP64 one to rounding (a synthetic matrix whose spectrum decays
-    exponentially over six decades, the shape of Fig. 7, staying above the
-    precision form's cutoff of 1e-7 sigma_max)."""
+    equals the FP64 one to the accuracy of its FP64-class products (a
+    synthetic matrix whose spectrum decays exponentially over six decades,
+    the shape of Fig. 7, staying above the precision form's cutoff of
+    1e-7 sigma_max)."""
     r, c = 300, 700
     U = np.linalg.qr(random_complex((r, r), 5))[0]
     Vh = np.linalg.qr(random_complex((c, r), 6))[0].conj().T
     s = np.exp(-np.linspace(0, 13.8, r))
     A = (U * s) @ Vh
     err, iso, lam2, l2ref = check_kept(M, A, r)
-    assert err < 1e-12
+    assert err < 1e-10
     assert len(lam2) == r
     # squared singular values from the FP64 Gram of the projection: to ~1e-13
     # of the largest (eps_64 times a few sqrt(m)), so relative 1e-9 down to
