@@ -5,8 +5,8 @@
 //   Q <- the m leading columns of the FP32 left factor, promoted to FP64 and
 //        made orthonormal by Newton-Schulz steps Q <- Q (3 I - Q^H Q) / 2;
 //   subspace iteration Q <- orth(A A^H Q), orth = shifted CholeskyQR3;
-//   Rayleigh-Ritz: B = Q^H A, FP64 one-sided Jacobi SVD B = U_B Lambda W^H,
-//        left factor Q U_B, rows Lambda W^H.
+//   Rayleigh-Ritz: Q turned towards the FP32 basis, B = Q^H A, FP64 one-sided
+//        Jacobi SVD B = U_B Lambda W^H, left factor Q U_B, rows Lambda W^H.
 //
 // The products are the engine's complex GEMM; these kernels convert, gather,
 // form the Newton-Schulz multiplier, factor the diagonal blocks of the
@@ -50,21 +50,23 @@ __global__ void ns_multiplier_kernel(double2* __restrict__ G, int m) {
 }
 
 // ---------------------------------------------------------------------------
-// Blocked Cholesky factorisation G = L L^H of an m x m Hermitian positive
-// definite complex128 matrix (row-major, leading dimension ldg, lower
-// triangle used), right-looking with CHOL_NB-wide panels (Golub & Van Loan,
-// Matrix Computations, Sec. 4.2): per panel, this kernel factors the
-// diagonal block in shared memory and inverts its triangular factor; the
-// panel solve and the trailing update are GEMMs issued by the host. A
-// non-positive pivot sets *status (the factorisation then continues with a
-// tiny pivot so that no NaN is produced).
+// Cholesky factorisation G = L L^H of a Hermitian positive definite
+// complex128 matrix with the inverse L^{-1} alongside, by recursive halving
+// (the host issues the off-diagonal GEMMs): this kernel is the base case, a
+// diagonal block of at most CHOL_NB rows factored in shared memory (Golub &
+// Van Loan, Matrix Computations, Sec. 4.2) whose triangular factor is then
+// inverted by forward substitution; L goes to the lower triangle of the
+// block in G (leading dimension ldg), L^{-1} to Linv (leading dimension ldl,
+// zeros above the diagonal). A non-positive pivot sets *status (the
+// factorisation then continues with a tiny pivot so that no NaN is
+// produced).
 // ---------------------------------------------------------------------------
-constexpr int CHOL_NB = 64;
+constexpr int CHOL_NB = 32;
 constexpr int CHOL_LD = CHOL_NB + 1;
 constexpr int CHOL_SMEM = 2 * CHOL_NB * CHOL_LD * (int)sizeof(double2);
 
 __global__ void __launch_bounds__(256) chol_diag_kernel(double2* __restrict__ G, int ldg, int k0, int b,
-                                                        double2* __restrict__ Linv, int* __restrict__ status) {
+                                                        double2* __restrict__ Linv, int ldl, int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char csm[];
   double2* Ls = reinterpret_cast<double2*>(csm);            // [NB][LD]
   double2* Xs = Ls + CHOL_NB * CHOL_LD;                      // [NB][LD]
@@ -119,7 +121,7 @@ __global__ void __launch_bounds__(256) chol_diag_kernel(double2* __restrict__ G,
   for (int e = tid; e < b * b; e += blockDim.x) {
     const int i = e / b, j = e % b;
     if (i >= j) G[(size_t)(k0 + i) * ldg + k0 + j] = Ls[i * CHOL_LD + j];
-    Linv[(size_t)i * CHOL_NB + j] = Xs[i * CHOL_LD + j];
+    Linv[(size_t)i * ldl + j] = Xs[i * CHOL_LD + j];
   }
 }
 

@@ -135,12 +135,12 @@ struct mpo_ctx {
   double2 *mx_Q = nullptr, *mx_Q2 = nullptr, *mx_B = nullptr, *mx_T = nullptr;
   double2 *mx_V = nullptr, *mx_G = nullptr;
   double* mx_w = nullptr;
-  OSCtl* mx_osctl = nullptr;       // control block of the FP64 Rayleigh-Ritz SVD
-  double2 *mx_linv = nullptr, *mx_ptmp = nullptr;   // Cholesky: diagonal-block inverses, panel scratch
+  double2 *mx_Li = nullptr, *mx_ptmp = nullptr;     // Cholesky: the inverse factor, scratch of the recursion
+  double2* mx_Q0 = nullptr;        // the FP32 basis, kept for the alignment before Rayleigh-Ritz
+  OSCtl* mx_eosctl = nullptr;      // control block of the FP64 Rayleigh-Ritz SVD
   int* mx_chst = nullptr;          // set when a Cholesky pivot was not positive
   OzWork oz;                       // FP64-accurate tensor-core GEMM scratch (precision form)
   bool use_oz = false;
-  struct MxSync { GridCtl g32; GridCtl eig[8]; };
   bool prof = false;
   struct Pending { int cls; cudaEvent_t a, b; double flops, bytes; };
   std::vector<Pending> pend;
@@ -417,7 +417,9 @@ static void free_oz(OzWork& w) {
 }
 
 // Products large enough to fill 128 x 128 real tiles go to the tensor cores.
-static bool oz_worth(int M, int N, int K) { return (double)M * N * K >= 1.6e7 && M >= 32 && N >= 16 && K >= 32; }
+// (SIMT FP64 runs at about 8 GFLOP/s per SM on this part, so even small
+// products with few tiles are faster as split BF16 products.)
+static bool oz_worth(int M, int N, int K) { return (double)M * N * K >= 2.6e5 && M >= 16 && N >= 8 && K >= 16; }
 
 static cudaError_t mx_gemm(mpo_ctx* h, int M, int N, int K, const double2* A, int lda, int opA, const double2* B,
                            int ldb, int opB, double2* C, int ldc, double alpha = 1.0, int accumulate = 0) {
@@ -446,58 +448,57 @@ static int mx_orthonormalise(mpo_ctx* h, int r, int m) {
   return MPO_OK;
 }
 
-// G (m x m, leading dimension m) = L L^H in place (lower triangle), blocked
-// right-looking: per CHOL_NB panel the diagonal block is factored (and its
-// factor inverted) by chol_diag_kernel, the panel below becomes
-// G21 L11^{-H} and the trailing block is updated by G22 -= P P^H.
-static int mx_cholesky(mpo_ctx* h, double2* G, int m) {
-  CK(h, ensure_dynamic_smem((const void*)chol_diag_kernel, CHOL_SMEM));
-  for (int k0 = 0; k0 < m; k0 += CHOL_NB) {
-    const int b = std::min(CHOL_NB, m - k0);
-    double2* Li = h->mx_linv + (size_t)(k0 / CHOL_NB) * CHOL_NB * CHOL_NB;
-    {
-      ProfScope ps(h, PK_REFINE, 8.0 * b * b * b / 3.0, 2.0 * b * b * sizeof(double2));
-      chol_diag_kernel<<<1, 256, CHOL_SMEM, h->st>>>(G, m, k0, b, Li, h->mx_chst);
-      CK(h, cudaGetLastError());
-    }
-    const int rest = m - k0 - b;
-    if (rest > 0) {
-      CK(h, mx_gemm(h, rest, b, b, G + (size_t)(k0 + b) * m + k0, m, 0, Li, CHOL_NB, 1, h->mx_ptmp, CHOL_NB));
-      CK(h, cudaMemcpy2DAsync(G + (size_t)(k0 + b) * m + k0, (size_t)m * sizeof(double2), h->mx_ptmp,
-                              CHOL_NB * sizeof(double2), (size_t)b * sizeof(double2), rest, cudaMemcpyDeviceToDevice,
-                              h->st));
-      CK(h, mx_gemm(h, rest, rest, b, h->mx_ptmp, CHOL_NB, 0, h->mx_ptmp, CHOL_NB, 1, G + (size_t)(k0 + b) * (m + 1), m,
-                    -1.0, 1));
-    }
+// Cholesky factorisation of the Hermitian block G[k0:k0+s, k0:k0+s]
+// (leading dimension m) into L (lower triangle, in place) and L^{-1} into the
+// same block of Li, by recursive halving: with G = [[A11, .], [A21, A22]],
+//   L11, L11^{-1} <- recursion on A11;  L21 = A21 L11^{-H};
+//   A22 -= L21 L21^H;  L22, L22^{-1} <- recursion on A22;
+//   (L^{-1})_21 = -L22^{-1} L21 L11^{-1}.
+// Blocks of at most CHOL_NB rows are factored by chol_diag_kernel; the rest
+// is GEMMs, which grow with the block and run on the tensor cores.
+static int mx_chol_rec(mpo_ctx* h, double2* G, double2* Li, int m, int k0, int s) {
+  if (s <= CHOL_NB) {
+    ProfScope ps(h, PK_REFINE, 8.0 * s * s * s / 3.0, 2.0 * s * s * sizeof(double2));
+    chol_diag_kernel<<<1, 256, CHOL_SMEM, h->st>>>(G, m, k0, s, Li + (size_t)k0 * m + k0, m, h->mx_chst);
+    CK(h, cudaGetLastError());
+    return MPO_OK;
   }
+  const int s1 = std::min(s - 1, (s / 2 + CHOL_NB - 1) / CHOL_NB * CHOL_NB), s2 = s - s1;
+  int rc = mx_chol_rec(h, G, Li, m, k0, s1);
+  if (rc) return rc;
+  double2* A21 = G + (size_t)(k0 + s1) * m + k0;
+  double2* A22 = G + (size_t)(k0 + s1) * m + k0 + s1;
+  const double2* Li11 = Li + (size_t)k0 * m + k0;
+  double2* Li21 = Li + (size_t)(k0 + s1) * m + k0;
+  const double2* Li22 = Li + (size_t)(k0 + s1) * m + k0 + s1;
+  double2* T = h->mx_ptmp;                                                     // s2 x s1
+  CK(h, mx_gemm(h, s2, s1, s1, A21, m, 0, Li11, m, 1, T, s1));               // L21 = A21 L11^{-H}
+  CK(h, cudaMemcpy2DAsync(A21, (size_t)m * sizeof(double2), T, (size_t)s1 * sizeof(double2),
+                          (size_t)s1 * sizeof(double2), s2, cudaMemcpyDeviceToDevice, h->st));
+  CK(h, mx_gemm(h, s2, s2, s1, A21, m, 0, A21, m, 1, A22, m, -1.0, 1));      // A22 -= L21 L21^H
+  rc = mx_chol_rec(h, G, Li, m, k0 + s1, s2);
+  if (rc) return rc;
+  CK(h, mx_gemm(h, s2, s1, s1, A21, m, 0, Li11, m, 0, T, s1));               // L21 L11^{-1}
+  CK(h, mx_gemm(h, s2, s1, s2, Li22, m, 0, T, s1, 0, Li21, m, -1.0, 0));    // -L22^{-1} (.)
   return MPO_OK;
 }
 
-// Y (r x m, leading dimension m) <- Y L^{-H} in place, L the Cholesky factor
-// in G: column block J becomes (Y_J - Y_{<J} L_{J,<J}^H) L_JJ^{-H}.
-static int mx_trsm(mpo_ctx* h, double2* Y, int r, int m, const double2* G) {
-  for (int j0 = 0; j0 < m; j0 += CHOL_NB) {
-    const int b = std::min(CHOL_NB, m - j0);
-    if (j0 > 0) CK(h, mx_gemm(h, r, b, j0, Y, m, 0, G + (size_t)j0 * m, m, 1, Y + j0, m, -1.0, 1));
-    CK(h, mx_gemm(h, r, b, b, Y + j0, m, 0, h->mx_linv + (size_t)(j0 / CHOL_NB) * CHOL_NB * CHOL_NB, CHOL_NB, 1,
-                  h->mx_ptmp, CHOL_NB));
-    CK(h, cudaMemcpy2DAsync(Y + j0, (size_t)m * sizeof(double2), h->mx_ptmp, CHOL_NB * sizeof(double2),
-                            (size_t)b * sizeof(double2), r, cudaMemcpyDeviceToDevice, h->st));
-  }
-  return MPO_OK;
-}
-
-// Y (r x m) <- an orthonormal basis of its span by Cholesky QR: G = Y^H Y
-// (+ shift_rel * trace(G) on the diagonal), G = L L^H, Y <- Y L^{-H}.
-static int mx_cholqr(mpo_ctx* h, double2* Y, int r, int m, double shift_rel) {
-  CK(h, mx_gemm(h, m, m, r, Y, m, 1, Y, m, 0, h->mx_G, m));
+// Y (rows x m, leading dimension m) <- an orthonormal basis of its span by
+// Cholesky QR: G = Y^H Y (+ shift_rel * trace(G) on the diagonal),
+// G = L L^H, result Y L^{-H}, written to `spare` and swapped with Y.
+static int mx_cholqr(mpo_ctx* h, double2*& Y, double2*& spare, int rows, int m, double shift_rel) {
+  CK(h, mx_gemm(h, m, m, rows, Y, m, 1, Y, m, 0, h->mx_G, m));
   if (shift_rel > 0.0) {
     add_trace_shift_kernel<<<1, 1024, 0, h->st>>>(h->mx_G, m, shift_rel);
     CK(h, cudaGetLastError());
   }
-  int rc = mx_cholesky(h, h->mx_G, m);
+  CK(h, cudaMemsetAsync(h->mx_Li, 0, (size_t)m * m * sizeof(double2), h->st));
+  CK(h, ensure_dynamic_smem((const void*)chol_diag_kernel, CHOL_SMEM));
+  int rc = mx_chol_rec(h, h->mx_G, h->mx_Li, m, 0, m);
   if (rc) return rc;
-  return mx_trsm(h, Y, r, m, h->mx_G);
+  CK(h, mx_gemm(h, rows, m, m, Y, m, 0, h->mx_Li, m, 1, spare, m));          // Y L^{-H}
+  std::swap(Y, spare);
+  return MPO_OK;
 }
 
 // Shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto & Yanagisawa,
@@ -507,24 +508,12 @@ static int mx_cholqr(mpo_ctx* h, double2* Y, int r, int m, double shift_rel) {
 // products: FP64's, or 2^-40 for the tensor-core split products (their
 // error is about 2^-42 of |row| |column|), so that the shift dominates the
 // Gram matrix's own error and every pivot stays positive.
-static int mx_scholqr3(mpo_ctx* h, double2* Y, int r, int m) {
+static int mx_scholqr3(mpo_ctx* h, double2*& Y, double2*& spare, int r, int m) {
   const double u = h->use_oz ? 9.094947017729282e-13 : 1.1102230246251565e-16;
-  int rc = mx_cholqr(h, Y, r, m, 11.0 * ((double)r * m + (double)m * (m + 1)) * u);
-  if (!rc) rc = mx_cholqr(h, Y, r, m, 0.0);
-  if (!rc) rc = mx_cholqr(h, Y, r, m, 0.0);
+  int rc = mx_cholqr(h, Y, spare, r, m, 11.0 * ((double)r * m + (double)m * (m + 1)) * u);
+  if (!rc) rc = mx_cholqr(h, Y, spare, r, m, 0.0);
+  if (!rc) rc = mx_cholqr(h, Y, spare, r, m, 0.0);
   return rc;
-}
-
-// Rayleigh-Ritz in FP64: B = Q^H X (m x c), then the FP64 one-sided (row)
-// Jacobi SVD of B, B = U_B B' with the rows of B' = Lambda W^H mutually
-// orthogonal; squared row norms -> h->mx_w, U_B^T -> h->mx_V. Working on B
-// itself (not on B B^H) keeps the singular values' relative accuracy.
-static int mx_ritz(mpo_ctx* h, const double2* X, int r, int c, int ldx, int m, int slot) {
-  CK(h, mx_gemm(h, m, c, r, h->mx_Q, m, 1, X, ldx, 0, h->mx_B, c));
-  ProfScope ps(h, PK_EIG64, 13.3 * (double)m * m * m, (2.0 * m * c + (double)m * m) * sizeof(double2));
-  CK(h, launch_onesided<double>(h->st, h->mx_B, m, c, c, h->mx_V, h->mx_w, h->mx_osctl + slot,
-                                h->opts.eig_max_sweeps, h->opts.barrier_timeout_s, h->num_sms));
-  return MPO_OK;
 }
 
 static int msvd_select(mpo_ctx* h, double2* X, int r, int c, int ldx, int cap, bool disc, double* S, double* sch, int* k) {
@@ -568,23 +557,43 @@ static int msvd_select(mpo_ctx* h, double2* X, int r, int c, int ldx, int cap, b
   }
   int rc = mx_orthonormalise(h, r, m);
   if (rc) return rc;
+  if (steps > 0)
+    CK(h, cudaMemcpyAsync(h->mx_Q0, h->mx_Q, (size_t)r * m * sizeof(double2), cudaMemcpyDeviceToDevice, h->st));
   // 3. subspace iteration in FP64, orthonormalising after each of the two
   // products (W <- orth(X^H Q), Q <- orth(X W)), so that each basis has
   // condition number sigma_1 / sigma_m rather than its square
   for (int it = 0; it < steps; ++it) {
     CK(h, mx_gemm(h, c, m, r, X, ldx, 1, h->mx_Q, m, 0, h->mx_T, m));     // T = X^H Q (c x m)
-    rc = mx_scholqr3(h, h->mx_T, c, m);
+    rc = mx_scholqr3(h, h->mx_T, h->mx_B, c, m);
     if (rc) return rc;
     CK(h, mx_gemm(h, r, m, c, X, ldx, 0, h->mx_T, m, 0, h->mx_Q2, m));    // X T (r x m)
     std::swap(h->mx_Q, h->mx_Q2);
-    rc = mx_scholqr3(h, h->mx_Q, r, m);
+    rc = mx_scholqr3(h, h->mx_Q, h->mx_Q2, r, m);
     if (rc) return rc;
   }
-  // 4. Rayleigh-Ritz projection and the outputs in the one-sided Jacobi convention
-  rc = mx_ritz(h, X, r, c, ldx, m, 0);
-  if (rc) return rc;
+  // 4. Rayleigh-Ritz on span(Q). The refined basis is first turned towards
+  // the FP32 singular vectors, Q <- Q W with W the orthonormal factor of
+  // G = Q^H Q0 (m x m; shifted CholeskyQR3 of G, so W is unitary to rounding
+  // whatever the conditioning of G), so that the rows of B = Q^H X start
+  // nearly orthogonal; then the FP64 one-sided (row) Jacobi SVD of B,
+  // B = U_B Lambda W^H, which keeps the small singular values' relative
+  // accuracy (no Gram matrix). Q U_B is the left factor.
+  if (steps > 0) {
+    double2 *Wm = h->mx_T, *Wspare = h->mx_B;                                // m x m in buffers of c x m
+    CK(h, mx_gemm(h, m, m, r, h->mx_Q, m, 1, h->mx_Q0, m, 0, Wm, m));         // G = Q^H Q0
+    rc = mx_scholqr3(h, Wm, Wspare, m, m);
+    if (rc) return rc;
+    CK(h, mx_gemm(h, r, m, m, h->mx_Q, m, 0, Wm, m, 0, h->mx_Q2, m));         // Q W
+    std::swap(h->mx_Q, h->mx_Q2);
+  }
+  CK(h, mx_gemm(h, m, c, r, h->mx_Q, m, 1, X, ldx, 0, h->mx_B, c));        // B = Q^H X
+  {
+    ProfScope ps(h, PK_EIG64, 13.3 * (double)m * m * m, (2.0 * m * c + (double)m * m) * sizeof(double2));
+    CK(h, launch_onesided<double>(h->st, h->mx_B, m, c, c, h->mx_V, h->mx_w, h->mx_eosctl, h->opts.eig_max_sweeps,
+                                  h->opts.barrier_timeout_s, h->num_sms));
+  }
   // left factor Q U_B, stored as rows conj(column j) = U_B^H Q^H with
-  // U_B^H = conj(U_B^T); the rows Lambda W^H of B' go to X
+  // U_B^H = conj(U_B^T); the rows Lambda W^H of the rotated B go to X
   {
     ProfScope ps(h, PK_REFINE, 0.0, 2.0 * m * m * sizeof(double2));
     conj_inplace_kernel<<<grid_for((size_t)m * m, h->num_sms), 256, 0, h->st>>>(h->mx_V, (size_t)m * m);
@@ -601,8 +610,8 @@ static int msvd_select(mpo_ctx* h, double2* X, int r, int c, int ldx, int cap, b
   }
   CK(h, cudaMemcpyAsync(&h->hs->info, h->info, sizeof(SelectInfo), cudaMemcpyDeviceToHost, h->st));
   CK(h, cudaMemcpyAsync(&h->hs->ctl, &h->osctl->g, sizeof(GridCtl), cudaMemcpyDeviceToHost, h->st));
-  CK(h, cudaMemcpyAsync(h->hs->eig, &h->mx_osctl->g, sizeof(GridCtl), cudaMemcpyDeviceToHost, h->st));
   CK(h, cudaMemcpyAsync(&h->hs->chol_status, h->mx_chst, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(h, cudaMemcpyAsync(h->hs->eig, &h->mx_eosctl->g, sizeof(GridCtl), cudaMemcpyDeviceToHost, h->st));
   if (h->use_oz) CK(h, cudaMemcpyAsync(&h->hs->oz_err, h->oz.status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
   if (h->prof) CK(h, cudaMemcpyAsync(h->hs->phase_ns, h->osctl->phase_ns, sizeof(h->hs->phase_ns), cudaMemcpyDeviceToHost, h->st));
   CK(h, cudaStreamSynchronize(h->st));
@@ -618,6 +627,7 @@ static int msvd_select(mpo_ctx* h, double2* X, int r, int c, int ldx, int cap, b
   if (h->hs->eig[0].err) return fail(h, MPO_ERR_TIMEOUT, "grid barrier wait timed out in the FP64 Rayleigh-Ritz SVD");
   if (h->hs->eig[0].status)
     return fail(h, MPO_ERR_NOCONV, "FP64 Rayleigh-Ritz SVD reached eig_max_sweeps (m = " + std::to_string(m) + ")");
+
   *k = h->hs->info.k;
   return MPO_OK;
 }
@@ -1049,9 +1059,10 @@ static bool alloc_factor_ws(mpo_ctx* h, int m, int ccap, size_t bj_nch) {
     ok = ok && alloc((void**)&h->mx_V, mm * mm * sizeof(double2));
     ok = ok && alloc((void**)&h->mx_G, mm * mm * sizeof(double2));
     ok = ok && alloc((void**)&h->mx_w, mm * sizeof(double));
-    ok = ok && alloc((void**)&h->mx_osctl, sizeof(OSCtl));
-    ok = ok && alloc((void**)&h->mx_linv, (mm / CHOL_NB + 1) * CHOL_NB * CHOL_NB * sizeof(double2));
-    ok = ok && alloc((void**)&h->mx_ptmp, std::max<size_t>(std::max<size_t>(m, ccap), mm) * CHOL_NB * sizeof(double2));
+    ok = ok && alloc((void**)&h->mx_Li, mm * mm * sizeof(double2));
+    ok = ok && alloc((void**)&h->mx_eosctl, sizeof(OSCtl));
+    ok = ok && alloc((void**)&h->mx_Q0, (size_t)m * mm * sizeof(double2));
+    ok = ok && alloc((void**)&h->mx_ptmp, mm * mm * sizeof(double2));
     ok = ok && alloc((void**)&h->mx_chst, sizeof(int));
   }
   return ok;
@@ -1129,8 +1140,8 @@ int mpo_init(mpo_handle* out, int n, int chi_max, mpo_precision prec, void* stre
                                       2 * (size_t)m * h->mx_mcap * sizeof(double2) +
                                       2 * (size_t)mx_ccap * h->mx_mcap * sizeof(double2) +
                                       2 * (size_t)h->mx_mcap * h->mx_mcap * sizeof(double2) +
-                                      (size_t)std::max(std::max(m, mx_ccap), h->mx_mcap) * CHOL_NB * sizeof(double2) +
-                                      (size_t)h->mx_mcap * sizeof(double)
+                                      4 * (size_t)h->mx_mcap * h->mx_mcap * sizeof(double2) +
+                                      (size_t)m * h->mx_mcap * sizeof(double2) + (size_t)h->mx_mcap * sizeof(double)
                                 : 0) +
                       (h->use_oz ? (size_t)oz::S * 2 * 3 * (size_t)std::max(m, mx_ccap) * 2 *
                                        (size_t)((std::max(m, mx_ccap) + 127) / 128 * 128)
@@ -1202,8 +1213,8 @@ void mpo_free(mpo_handle h) {
   void* ps[] = {h->spare, h->theta, h->theta2, h->osctl, h->tc_status, h->bj_gpart, h->bj_j, h->bj_act, h->vecs, h->tmp, h->wv, h->perm, h->lam2, h->Ms, h->dgates,
                 h->dsup, h->dp, h->info, h->ctl, h->scal, h->dS, h->dschmidt, h->tv0, h->tv1,
                 h->mx_a32, h->mx_ut32, h->mx_w32, h->mx_perm32, h->mx_lam32, h->mx_info32, h->mx_Q, h->mx_Q2,
-                h->mx_B, h->mx_T, h->mx_V, h->mx_G, h->mx_w, h->mx_osctl,
-                h->mx_linv, h->mx_ptmp, h->mx_chst};
+                h->mx_B, h->mx_T, h->mx_V, h->mx_G, h->mx_w,
+                h->mx_Li, h->mx_ptmp, h->mx_chst, h->mx_eosctl, h->mx_Q0};
   for (void* p : ps) if (p) cudaFree(p);
   if (h->hs) cudaFreeHost(h->hs);
   free_oz(h->oz);
