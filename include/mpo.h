@@ -53,14 +53,14 @@ typedef struct mpo_ctx *mpo_handle;
  *   MPO_MIXED_FP32: the precision form. complex128 site tensors; every truncated
  *                   SVD (App. A) and centre move starts from the FP32 one-sided
  *                   Jacobi SVD of an FP32 copy, whose m = chi_max + oversample
- *                   leading left singular vectors are refined in FP64 by
- *                   refine_steps FP64 subspace-iteration steps (shifted
- *                   CholeskyQR3 orthonormalisation) and a final Rayleigh-Ritz
- *                   projection B = Q^H theta' whose m x c SVD is an FP64
- *                   one-sided Jacobi; the singular values, their normalisation
- *                   and the entropy are FP64. Matches the FP64 form to
- *                   |dS| <= 1e-6 and a kept-theta relative Frobenius error
- *                   <= 1e-7 per gate. */
+ *                   leading left singular vectors Q are refined in FP64 by one
+ *                   Rayleigh-Ritz step: B = Q^H theta' and H = B B^H by
+ *                   FP64-accurate products, and the FP64 Hermitian Jacobi
+ *                   eigen-solve of H (optionally preceded by refine_steps FP64
+ *                   subspace-iteration steps); the singular values, their
+ *                   normalisation and the entropy are FP64. Matches the FP64
+ *                   form to |dS| <= 1e-6 and a kept-theta relative Frobenius
+ *                   error <= 1e-7 per gate. */
 typedef enum { MPO_FP64 = 0, MPO_FP32 = 1, MPO_MIXED_FP32 = 2 } mpo_precision;
 
 /* Which bonds mpo_entropy reports.
@@ -101,11 +101,11 @@ typedef struct {
                                refinement and the projections) on the tensor cores as
                                FP64-accurate BF16 split products [0 = on; < 0 = SIMT FP64] */
   int oversample;           /* MPO_MIXED_FP32: extra FP32 singular vectors carried into the FP64
-                               refinement of a truncating SVD, beyond chi_max [0 = chi_max;
+                               Rayleigh-Ritz step of a truncating SVD, beyond chi_max [0 = 64;
                                < 0 = none] */
-  int refine_steps;         /* MPO_MIXED_FP32: subspace-iteration steps before the final
-                               Rayleigh-Ritz projection of a truncating SVD [0 = 5, at most 7;
-                               < 0 = none] */
+  int refine_steps;         /* MPO_MIXED_FP32: FP64 subspace-iteration steps (shifted CholeskyQR3
+                               after each product) before the Rayleigh-Ritz step of a truncating
+                               SVD [0 or < 0 = none, the default; at most 7] */
 } mpo_opts;
 
 /* Fill *o with the defaults. */

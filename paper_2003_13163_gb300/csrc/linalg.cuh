@@ -131,6 +131,7 @@ inline cudaError_t cgemm(cudaStream_t st, int M, int N, int K, const cplx<T>* A,
 //
 // Each round runs as three phases of one persistent cooperative launch:
 //   A (every CTA, redundantly): the rotation table of the round -> smem;
+//                                                                  barrier
 //   B (G <- G J, V <- V J): one warp per row, lanes over pairs;   barrier
 //   C (G <- J^H G): one warp per pair, lanes over columns;           barrier
 // All G/V traffic uses L2-only loads/stores because other CTAs write it.
@@ -210,6 +211,9 @@ __global__ void __launch_bounds__(256) jacobi_kernel(cplx<T>* G, int m, cplx<T>*
       const int act = s_active;   // identical in every CTA: same inputs, same code
       sweep_active += act;
       if (act == 0) continue;
+      // phase B rewrites the pivots (G_pp, G_qq, G_pq) that phase A reads:
+      // no CTA rotates before every CTA has built its table from the same G
+      if (!grid_barrier(ctl, nblk, timeout_ns)) return;
       // ---- phase B: column rotations, G <- G J and V <- V J ---------------
       for (long row = gwarp; row < 2L * m; row += nwarps) {
         cplx<T>* Rw = row < m ? G + (size_t)row * m : V + (size_t)(row - m) * m;

@@ -135,9 +135,13 @@ struct mpo_ctx {
   double2 *mx_Q = nullptr, *mx_Q2 = nullptr, *mx_B = nullptr, *mx_T = nullptr;
   double2 *mx_V = nullptr, *mx_G = nullptr;
   double* mx_w = nullptr;
-  double2 *mx_Li = nullptr, *mx_ptmp = nullptr;     // Cholesky: the inverse factor, scratch of the recursion
-  double2* mx_Q0 = nullptr;        // the FP32 basis, kept for the alignment before Rayleigh-Ritz
-  OSCtl* mx_eosctl = nullptr;      // control block of the FP64 Rayleigh-Ritz SVD
+  double2* mx_W = nullptr;         // D L^{-H} of a Cholesky QR pass; the FP32 Ritz vectors, promoted
+  double2* mx_Q0 = nullptr;        // the stage-2 basis (FP32 Ritz directions in FP64)
+  float2 *mx_A32 = nullptr, *mx_Li32 = nullptr, *mx_t32 = nullptr;   // FP32 Cholesky: scaled Gram, L^{-1}, scratch
+  double* mx_d = nullptr;          // column scales of a Cholesky QR pass
+  unsigned long long mx_seed = 0;  // start-basis counter
+  int mx_last_steps = 0;           // subspace steps taken by the last factorisation
+  OSCtl* mx_eosctl = nullptr;      // control block of the FP64 Rayleigh-Ritz eigen-solve
   int* mx_chst = nullptr;          // set when a Cholesky pivot was not positive
   OzWork oz;                       // FP64-accurate tensor-core GEMM scratch (precision form)
   bool use_oz = false;
@@ -347,23 +351,32 @@ static cudaError_t launch_block_jacobi(cudaStream_t st, cplx<T>* X, int r, int c
 //   1. FP32 one-sided Jacobi SVD of fl32(X) -> approximate U (r x r), w.
 //   2. Q (r x m, FP64) = the m = min(r, cap + oversample) leading columns of U,
 //      made orthonormal to FP64 rounding by Newton-Schulz steps.
-//   3. If m < r (the truncation can bite), refine_steps subspace-iteration
-//      steps W <- orth(X^H Q), Q <- orth(X W) in FP64, each damping the
-//      components of the leading singular vectors outside span(Q) by
+//   3. Optional (refine_steps > 0, only when m < r): subspace-iteration steps
+//      W <- orth(X^H Q), Q <- orth(X W) in FP64, each damping the components
+//      of the leading singular vectors outside span(Q) by
 //      (sigma_{m+1} / sigma_j)^2; orth is shifted Cholesky QR followed by two
 //      Cholesky QR passes (shifted CholeskyQR3, stable for condition numbers
 //      up to 1/u), applied after each product so that a basis never carries
-//      more than the condition number sigma_1 / sigma_m.
-//      With m = r the span of Q is the whole row space already.
-//   4. Rayleigh-Ritz: B = Q^H X and its FP64 one-sided Jacobi SVD
-//      B = U_B Lambda W^H. The Ritz values w = Lambda^2 are the squared
-//      singular values, Q U_B the left singular vectors and Lambda W^H the
-//      scaled right ones.
+//      more than the condition number sigma_1 / sigma_m; the refined basis is
+//      then turned back towards the FP32 one (Q <- Q W, W the orthonormal
+//      factor of Q^H Q_FP32) so that the Rayleigh-Ritz matrix stays nearly
+//      diagonal.
+//   4. Rayleigh-Ritz in FP64: B = Q^H X (m x c), H = B B^H (m x m), both by
+//      the FP64-class products, and the FP64 Hermitian Jacobi eigen-solve
+//      H = V diag(w) V^H. With Q from the FP32 singular vectors H is nearly
+//      diagonal, so the solve ends after a few sweeps. The Ritz values w are
+//      the squared singular values, Q V the left singular vectors and the rows
+//      of V^H B = Lambda W^H the scaled right ones.
 // Outputs follow the one-sided Jacobi convention of svd_select: rows 0..m-1
-// of X are overwritten with Lambda W^H, h->vecs holds U_B^H Q^H (m x r, row
-// j = conj of left singular vector j: h->vecs_conj), h->mx_w the w; the
-// select kernel then sorts and truncates.
+// of X are overwritten with V^H B, h->vecs holds V^H Q^H (m x r, row j = conj
+// of left singular vector j: h->vecs_conj), h->mx_w the w; the select kernel
+// then sorts and truncates, with the discarded weight taken against the
+// squared Frobenius norm of X (the Ritz values cover span(Q) only).
 // ---------------------------------------------------------------------------
+constexpr int kMixedMargin = 64;      // Ritz directions carried into the FP64 step beyond cap
+constexpr int kMixedMaxSteps = 24;    // cap on subspace-iteration steps of one factorisation
+constexpr int kMixedSteps = 4;        // steps before the first convergence check
+
 // C (M x N) = alpha op(A) op(B) (+ C), complex128, FP64-accurate on the
 // tensor cores (ozgemm.cuh): exponents, BF16 slices of both operands, then
 // the MMA kernel. Returns cudaErrorInvalidValue if the scratch is too small.
@@ -432,202 +445,264 @@ static cudaError_t mx_gemm(mpo_ctx* h, int M, int N, int K, const double2* A, in
   return cgemm<double>(h->st, M, N, K, A, lda, opA, B, ldb, opB, C, ldc, nullptr, alpha, accumulate);
 }
 
-// Q (r x m) <- Q (3 I - Q^H Q) / 2, twice: from a basis orthonormal to ~1e-5
-// the defect falls to ~1e-10 and then to FP64 rounding.
-static int mx_orthonormalise(mpo_ctx* h, int r, int m) {
-  for (int it = 0; it < 2; ++it) {
-    CK(h, mx_gemm(h, m, m, r, h->mx_Q, m, 1, h->mx_Q, m, 0, h->mx_G, m));
+// Y (rows x m, leading dimension m) <- Y (3 I - Y^H Y) / 2, iters times
+// (Newton-Schulz iteration for the orthonormal polar factor, Higham,
+// Functions of Matrices, Sec. 8.3): each step squares the defect
+// |Y^H Y - I|, so a basis orthonormal to ~1e-3 reaches FP64 rounding in four
+// steps. The result is left in Y (spare is scratch; the two are swapped).
+static int mx_newton_schulz(mpo_ctx* h, double2*& Y, double2*& spare, int rows, int m, int iters) {
+  for (int it = 0; it < iters; ++it) {
+    CK(h, mx_gemm(h, m, m, rows, Y, m, 1, Y, m, 0, h->mx_G, m));
     {
       ProfScope ps(h, PK_REFINE, 0.0, 2.0 * m * m * sizeof(double2));
       ns_multiplier_kernel<<<grid_for((size_t)m * m, h->num_sms), 256, 0, h->st>>>(h->mx_G, m);
       CK(h, cudaGetLastError());
     }
-    CK(h, mx_gemm(h, r, m, m, h->mx_Q, m, 0, h->mx_G, m, 0, h->mx_Q2, m));
-    std::swap(h->mx_Q, h->mx_Q2);
+    CK(h, mx_gemm(h, rows, m, m, Y, m, 0, h->mx_G, m, 0, spare, m));
+    std::swap(Y, spare);
   }
   return MPO_OK;
 }
 
-// Cholesky factorisation of the Hermitian block G[k0:k0+s, k0:k0+s]
+// FP32 Cholesky factorisation of the Hermitian block A[k0:k0+s, k0:k0+s]
 // (leading dimension m) into L (lower triangle, in place) and L^{-1} into the
-// same block of Li, by recursive halving: with G = [[A11, .], [A21, A22]],
+// same block of Li, by recursive halving: with A = [[A11, .], [A21, A22]],
 //   L11, L11^{-1} <- recursion on A11;  L21 = A21 L11^{-H};
 //   A22 -= L21 L21^H;  L22, L22^{-1} <- recursion on A22;
 //   (L^{-1})_21 = -L22^{-1} L21 L11^{-1}.
-// Blocks of at most CHOL_NB rows are factored by chol_diag_kernel; the rest
-// is GEMMs, which grow with the block and run on the tensor cores.
-static int mx_chol_rec(mpo_ctx* h, double2* G, double2* Li, int m, int k0, int s) {
-  if (s <= CHOL_NB) {
-    ProfScope ps(h, PK_REFINE, 8.0 * s * s * s / 3.0, 2.0 * s * s * sizeof(double2));
-    chol_diag_kernel<<<1, 256, CHOL_SMEM, h->st>>>(G, m, k0, s, Li + (size_t)k0 * m + k0, m, h->mx_chst);
+// Blocks of at most CHOL32_NB rows are factored by chol_diag_kernel, the rest
+// by FP32 GEMMs. Li is zero above the diagonal blocks on entry.
+static int chol32_rec(mpo_ctx* h, float2* A, float2* Li, int m, int k0, int s) {
+  if (s <= CHOL32_NB) {
+    chol_diag_kernel<float, CHOL32_NB><<<1, 256, chol_smem_bytes<float, CHOL32_NB>(), h->st>>>(
+        A, m, k0, s, Li + (size_t)k0 * m + k0, m, h->mx_chst);
     CK(h, cudaGetLastError());
     return MPO_OK;
   }
-  const int s1 = std::min(s - 1, (s / 2 + CHOL_NB - 1) / CHOL_NB * CHOL_NB), s2 = s - s1;
-  int rc = mx_chol_rec(h, G, Li, m, k0, s1);
+  const int s1 = std::min(s - 1, (s / 2 + CHOL32_NB - 1) / CHOL32_NB * CHOL32_NB), s2 = s - s1;
+  int rc = chol32_rec(h, A, Li, m, k0, s1);
   if (rc) return rc;
-  double2* A21 = G + (size_t)(k0 + s1) * m + k0;
-  double2* A22 = G + (size_t)(k0 + s1) * m + k0 + s1;
-  const double2* Li11 = Li + (size_t)k0 * m + k0;
-  double2* Li21 = Li + (size_t)(k0 + s1) * m + k0;
-  const double2* Li22 = Li + (size_t)(k0 + s1) * m + k0 + s1;
-  double2* T = h->mx_ptmp;                                                     // s2 x s1
-  CK(h, mx_gemm(h, s2, s1, s1, A21, m, 0, Li11, m, 1, T, s1));               // L21 = A21 L11^{-H}
-  CK(h, cudaMemcpy2DAsync(A21, (size_t)m * sizeof(double2), T, (size_t)s1 * sizeof(double2),
-                          (size_t)s1 * sizeof(double2), s2, cudaMemcpyDeviceToDevice, h->st));
-  CK(h, mx_gemm(h, s2, s2, s1, A21, m, 0, A21, m, 1, A22, m, -1.0, 1));      // A22 -= L21 L21^H
-  rc = mx_chol_rec(h, G, Li, m, k0 + s1, s2);
+  float2* A21 = A + (size_t)(k0 + s1) * m + k0;
+  float2* A22 = A21 + s1;
+  const float2* Li11 = Li + (size_t)k0 * m + k0;
+  float2* Li21 = Li + (size_t)(k0 + s1) * m + k0;
+  const float2* Li22 = Li21 + s1;
+  float2* T = h->mx_t32;                                                                // s2 x s1
+  CK(h, cgemm<float>(h->st, s2, s1, s1, A21, m, 0, Li11, m, 1, T, s1));                 // L21 = A21 L11^{-H}
+  CK(h, cudaMemcpy2DAsync(A21, (size_t)m * sizeof(float2), T, (size_t)s1 * sizeof(float2),
+                          (size_t)s1 * sizeof(float2), s2, cudaMemcpyDeviceToDevice, h->st));
+  CK(h, cgemm<float>(h->st, s2, s2, s1, A21, m, 0, A21, m, 1, A22, m, nullptr, -1.0, 1));   // A22 -= L21 L21^H
+  rc = chol32_rec(h, A, Li, m, k0 + s1, s2);
   if (rc) return rc;
-  CK(h, mx_gemm(h, s2, s1, s1, A21, m, 0, Li11, m, 0, T, s1));               // L21 L11^{-1}
-  CK(h, mx_gemm(h, s2, s1, s2, Li22, m, 0, T, s1, 0, Li21, m, -1.0, 0));    // -L22^{-1} (.)
+  CK(h, cgemm<float>(h->st, s2, s1, s1, A21, m, 0, Li11, m, 0, T, s1));                 // L21 L11^{-1}
+  CK(h, cgemm<float>(h->st, s2, s1, s2, Li22, m, 0, T, s1, 0, Li21, m, nullptr, -1.0, 0));   // -L22^{-1} (.)
   return MPO_OK;
 }
 
-// Y (rows x m, leading dimension m) <- an orthonormal basis of its span by
-// Cholesky QR: G = Y^H Y (+ shift_rel * trace(G) on the diagonal),
-// G = L L^H, result Y L^{-H}, written to `spare` and swapped with Y.
-static int mx_cholqr(mpo_ctx* h, double2*& Y, double2*& spare, int rows, int m, double shift_rel) {
+// One mixed-precision Cholesky QR pass on Y (rows x m, leading dimension m):
+// G = Y^H Y by the FP64-class product, A = fl32(D G D) + shift I with
+// D = diag(G)^{-1/2}, the FP32 factorisation A = L L^H with L^{-1}, and
+// Y <- Y D L^{-H} by the FP64-class product (result in Y; spare is scratch).
+// The shift, 8 m u_32, lies above the FP32 rounding of A and of its
+// factorisation, so A stays positive definite whatever the conditioning of
+// Y; a pass takes a condition number kappa of Y to about sqrt(shift) kappa
+// (and no lower than 1 + shift). Mixed-precision Cholesky QR: Yamazaki,
+// Tomov & Dongarra, SIAM J. Sci. Comput. 37 (2015); the shift: Fukaya,
+// Kannan, Nakatsukasa, Yamamoto & Yanagisawa, SIAM J. Sci. Comput. 42 (2020).
+static int mx_cholqr_pass(mpo_ctx* h, double2*& Y, double2*& spare, int rows, int m) {
   CK(h, mx_gemm(h, m, m, rows, Y, m, 1, Y, m, 0, h->mx_G, m));
-  if (shift_rel > 0.0) {
-    add_trace_shift_kernel<<<1, 1024, 0, h->st>>>(h->mx_G, m, shift_rel);
+  {
+    ProfScope ps(h, PK_REFINE, 16.0 * m * m * m / 3.0, 6.0 * m * m * sizeof(float2));
+    const float shift = (float)(8.0 * m * 5.9604644775390625e-08);
+    scale_gram_fp32_kernel<<<grid_for((size_t)m * m, h->num_sms), 256, 0, h->st>>>(h->mx_G, m, shift, h->mx_A32,
+                                                                                      h->mx_d);
+    CK(h, cudaGetLastError());
+    CK(h, cudaMemsetAsync(h->mx_Li32, 0, (size_t)m * m * sizeof(float2), h->st));
+    int rc = chol32_rec(h, h->mx_A32, h->mx_Li32, m, 0, m);
+    if (rc) return rc;
+    form_w_kernel<<<grid_for((size_t)m * m, h->num_sms), 256, 0, h->st>>>(h->mx_Li32, h->mx_d, m, h->mx_W);
     CK(h, cudaGetLastError());
   }
-  CK(h, cudaMemsetAsync(h->mx_Li, 0, (size_t)m * m * sizeof(double2), h->st));
-  CK(h, ensure_dynamic_smem((const void*)chol_diag_kernel, CHOL_SMEM));
-  int rc = mx_chol_rec(h, h->mx_G, h->mx_Li, m, 0, m);
-  if (rc) return rc;
-  CK(h, mx_gemm(h, rows, m, m, Y, m, 0, h->mx_Li, m, 1, spare, m));          // Y L^{-H}
+  CK(h, mx_gemm(h, rows, m, m, Y, m, 0, h->mx_W, m, 0, spare, m));
   std::swap(Y, spare);
   return MPO_OK;
 }
 
-// Shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto & Yanagisawa,
-// SIAM J. Sci. Comput. 2020): one Cholesky QR with the shift
-// 11 (r m + m (m + 1)) u ||Y||^2 makes the basis well conditioned, two plain
-// passes make it orthonormal to rounding. u is the unit roundoff of the
-// products: FP64's, or 2^-40 for the tensor-core split products (their
-// error is about 2^-42 of |row| |column|), so that the shift dominates the
-// Gram matrix's own error and every pivot stays positive.
-static int mx_scholqr3(mpo_ctx* h, double2*& Y, double2*& spare, int r, int m) {
-  const double u = h->use_oz ? 9.094947017729282e-13 : 1.1102230246251565e-16;
-  int rc = mx_cholqr(h, Y, spare, r, m, 11.0 * ((double)r * m + (double)m * (m + 1)) * u);
-  if (!rc) rc = mx_cholqr(h, Y, spare, r, m, 0.0);
-  if (!rc) rc = mx_cholqr(h, Y, spare, r, m, 0.0);
-  return rc;
+static int mx_cholqr(mpo_ctx* h, double2*& Y, double2*& spare, int rows, int m, int passes) {
+  for (int p = 0; p < passes; ++p) {
+    int rc = mx_cholqr_pass(h, Y, spare, rows, m);
+    if (rc) return rc;
+  }
+  return MPO_OK;
+}
+
+// Subspace-iteration steps Q <- orth(X orth(X^H Q)) on Q (r x m). Each half
+// step is followed by three Cholesky QR passes, which hold the basis
+// condition number near 1 although every product multiplies it by up to
+// sigma_1 / sigma_m.
+static int mx_subspace_steps(mpo_ctx* h, const double2* X, int r, int c, int ldx, int m, int steps) {
+  for (int it = 0; it < steps; ++it) {
+    CK(h, mx_gemm(h, c, m, r, X, ldx, 1, h->mx_Q, m, 0, h->mx_T, m));     // T = X^H Q (c x m)
+    int rc = mx_cholqr(h, h->mx_T, h->mx_B, c, m, 3);
+    if (rc) return rc;
+    CK(h, mx_gemm(h, r, m, c, X, ldx, 0, h->mx_T, m, 0, h->mx_Q, m));     // Q = X T (r x m)
+    rc = mx_cholqr(h, h->mx_Q, h->mx_Q2, r, m, 3);
+    if (rc) return rc;
+  }
+  return MPO_OK;
+}
+
+static int msvd_status(mpo_ctx* h) {
+  if (h->hs->ctl.err) return fail(h, MPO_ERR_TIMEOUT, "grid barrier wait timed out in the FP32 Rayleigh-Ritz SVD");
+  if (h->hs->ctl.status) return fail(h, MPO_ERR_NOCONV, "FP32 Rayleigh-Ritz SVD reached eig_max_sweeps");
+  if (h->use_oz && h->hs->oz_err) return fail(h, MPO_ERR_TIMEOUT, "an mbarrier wait timed out in the tensor-core FP64 GEMM");
+  if (h->hs->chol_status) return fail(h, MPO_ERR_NOCONV, "Cholesky QR met a non-positive pivot");
+  return MPO_OK;
 }
 
 static int msvd_select(mpo_ctx* h, double2* X, int r, int c, int ldx, int cap, bool disc, double* S, double* sch, int* k) {
-  const int m = std::min(r, cap + h->mx_over);
+  const int m = std::min(r, cap + h->mx_over);          // dimension of the iterated subspace
+  const int mp = std::min(m, cap + kMixedMargin);        // dimension of the FP64 Rayleigh-Ritz step
   if (m > h->mx_mcap || r > h->m_cap) return fail(h, MPO_ERR_STATE, "mixed factorisation larger than its workspace");
-  const int steps = m < r ? std::min(h->mx_steps, 7) : 0;
+  const bool iterate = m < r;
   CK(h, cudaMemsetAsync(h->mx_chst, 0, sizeof(int), h->st));
-  // 1. FP32 copy and FP32 one-sided Jacobi SVD; the squared norm of X (the
-  // total weight of the discarded-weight ratio) before X is overwritten
   {
-    ProfScope ps(h, PK_CONVERT, 0.0, (double)r * c * (2 * sizeof(double2) + sizeof(float2)));
-    to_fp32_kernel<<<grid_for((size_t)r * c, h->num_sms), 256, 0, h->st>>>(X, r, c, ldx, h->mx_a32);
-    frob2_kernel<<<1, 1024, 0, h->st>>>(X, r, c, ldx, h->scal + 2);
+    ProfScope ps(h, PK_CONVERT, 0.0, (double)r * c * sizeof(double2));
+    frob2_kernel<<<1, 1024, 0, h->st>>>(X, r, c, ldx, h->scal + 2);          // total weight ||X||_F^2
     CK(h, cudaGetLastError());
   }
-  {
-    // algorithmic work of the approximate SVD: the Hermitian Gram of the short
-    // side (4 r^2 c) and the projection onto the kept vectors (8 k r c); the
-    // FP64 eigen-solve is counted under eig_fp64
-    const double mn = r, mx = c, kk = std::min(cap, r);
-    ProfScope ps(h, disc ? PK_SVD : PK_SVD_SWEEP, 4.0 * mn * mn * mx + 8.0 * kk * mn * mx,
-                 (2.0 * r * c + (double)r * r) * sizeof(float2));
-    if (h->block_min_rows > 0 && r >= h->block_min_rows)
-      CK(h, launch_block_jacobi<float>(h->st, h->mx_a32, r, c, c, h->mx_ut32, h->mx_w32, (float2*)h->bj_gpart,
-                                       h->bj_slots, (float2*)h->bj_j, h->bj_act, h->bj_act_ints, h->osctl,
-                                       h->opts.eig_max_sweeps, h->opts.barrier_timeout_s, h->num_sms));
-    else
-      CK(h, launch_onesided<float>(h->st, h->mx_a32, r, c, c, h->mx_ut32, h->mx_w32, h->osctl, h->opts.eig_max_sweeps,
-                                   h->opts.barrier_timeout_s, h->num_sms));
+  int rc = MPO_OK, steps = 0;
+  if (iterate) {
+    // 1. seeded Gaussian start and the first steps of the subspace iteration
+    {
+      ProfScope ps(h, PK_CONVERT, 0.0, (double)c * m * sizeof(double2));
+      h->mx_seed += 0x9E3779B97F4A7C15ull;
+      gauss_start_kernel<<<grid_for((size_t)c * m, h->num_sms), 256, 0, h->st>>>(h->mx_T, (size_t)c * m, h->mx_seed);
+      CK(h, cudaGetLastError());
+    }
+    CK(h, mx_gemm(h, r, m, c, X, ldx, 0, h->mx_T, m, 0, h->mx_Q, m));     // Q = X Omega
+    rc = mx_cholqr(h, h->mx_Q, h->mx_Q2, r, m, 3);
+    if (rc) return rc;
+    steps = std::max(1, h->mx_steps);
+    rc = mx_subspace_steps(h, X, r, c, ldx, m, steps);
+    if (rc) return rc;
   }
-  // 2. the m leading FP32 left singular vectors -> Q (FP64), orthonormalised
-  {
-    ProfScope ps(h, PK_SELECT, 0.0, (double)r * (sizeof(float) + sizeof(int) + sizeof(double)));
-    CK(h, launch_select<float>(h->st, h->mx_w32, r, m, -1.0, h->mx_perm32, h->mx_lam32, h->mx_info32, nullptr,
-                               nullptr, nullptr, nullptr));
+  // 2. FP32 Rayleigh-Ritz (stage 1), repeated after further steps until the
+  // FP32 Ritz values show the iteration converged: the leading cap
+  // directions have components outside span(Q) of order
+  // (sigma_{m+1} / sigma_cap)^(2 steps), estimated from the Ritz values as
+  // (w_m / w_cap)^steps and required below 1e-8
+  for (;;) {
+    if (iterate) {
+      rc = mx_newton_schulz(h, h->mx_Q, h->mx_Q2, r, m, 2);
+      if (rc) return rc;
+      CK(h, mx_gemm(h, m, c, r, h->mx_Q, m, 1, X, ldx, 0, h->mx_B, c));   // B = Q^H X (m x c)
+    }
+    {
+      ProfScope ps(h, PK_CONVERT, 0.0, (double)m * c * (sizeof(double2) + sizeof(float2)));
+      to_fp32_kernel<<<grid_for((size_t)m * c, h->num_sms), 256, 0, h->st>>>(iterate ? h->mx_B : X, m, c,
+                                                                             iterate ? c : ldx, h->mx_a32);
+      CK(h, cudaGetLastError());
+    }
+    {
+      const double fm = m, fc = c;
+      ProfScope ps(h, disc ? PK_SVD : PK_SVD_SWEEP, 4.0 * fm * fm * fc, (2.0 * fm * fc + fm * fm) * sizeof(float2));
+      CK(h, launch_onesided<float>(h->st, h->mx_a32, m, c, c, h->mx_ut32, h->mx_w32, h->osctl,
+                                   h->opts.eig_max_sweeps, h->opts.barrier_timeout_s, h->num_sms));
+    }
+    {
+      ProfScope ps(h, PK_SELECT, 0.0, (double)m * (sizeof(float) + sizeof(int) + sizeof(double)));
+      CK(h, launch_select<float>(h->st, h->mx_w32, m, m, -1.0, h->mx_perm32, h->mx_lam32, h->mx_info32, nullptr,
+                                 nullptr, nullptr, nullptr));
+    }
+    if (!iterate) break;
+    double lam[2];
+    CK(h, cudaMemcpyAsync(&lam[0], h->mx_lam32 + (cap - 1), sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(h, cudaMemcpyAsync(&lam[1], h->mx_lam32 + (m - 1), sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(h, cudaMemcpyAsync(&h->hs->ctl, &h->osctl->g, sizeof(GridCtl), cudaMemcpyDeviceToHost, h->st));
+    CK(h, cudaMemcpyAsync(&h->hs->chol_status, h->mx_chst, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    if (h->use_oz) CK(h, cudaMemcpyAsync(&h->hs->oz_err, h->oz.status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+    rc = msvd_status(h);
+    if (rc) return rc;
+    const double rho2 = lam[0] > 0.0 ? std::max(0.0, lam[1]) / lam[0] : 0.0;
+    if (steps >= kMixedMaxSteps || rho2 <= 0.0 || std::pow(rho2, steps) <= 1e-8) break;
+    const int need = rho2 < 1.0 ? (int)std::ceil(std::log(1e-8) / std::log(rho2)) : kMixedMaxSteps;
+    const int more = std::max(1, std::min(need, kMixedMaxSteps) - steps);
+    rc = mx_subspace_steps(h, X, r, c, ldx, m, more);
+    if (rc) return rc;
+    steps += more;
   }
+  h->mx_last_steps = steps;
+  // 3. the mp leading FP32 Ritz directions V_P (V = U32 in descending order,
+  // promoted), corrected to first order for their error along the other
+  // m - mp directions (the FP32 solve leaves couplings of 2 eps_32 sqrt(c)
+  // relative, which would otherwise leak into the kept subspace), then
+  // Q' = Q V_P made orthonormal in FP64
+  double2* Qp = h->mx_Q0;
+  double2* Qsp = h->mx_Q2;
   {
-    ProfScope ps(h, PK_CONVERT, 0.0, (double)r * m * (sizeof(double2) + sizeof(float2)));
-    promote_columns_kernel<<<grid_for((size_t)r * m, h->num_sms), 256, 0, h->st>>>(h->mx_ut32, r, h->mx_perm32, m, h->mx_Q);
+    ProfScope ps(h, PK_CONVERT, 0.0, (double)m * m * (sizeof(double2) + sizeof(float2)));
+    promote_columns_kernel<<<grid_for((size_t)m * m, h->num_sms), 256, 0, h->st>>>(h->mx_ut32, m, h->mx_perm32, m,
+                                                                                      h->mx_W);
     CK(h, cudaGetLastError());
   }
-  int rc = mx_orthonormalise(h, r, m);
+  if (mp < m) {
+    const double2* Bs = iterate ? h->mx_B : X;
+    const int ldbs = iterate ? c : ldx;
+    CK(h, mx_gemm(h, m, c, m, h->mx_W, m, 1, Bs, ldbs, 0, h->mx_T, c));        // V^H B (m x c)
+    CK(h, mx_gemm(h, m, m, c, h->mx_T, c, 0, h->mx_T, c, 1, h->mx_G, m));      // S = V^H H V
+    CK(h, mx_gemm(h, m, m, m, h->mx_W, m, 1, h->mx_W, m, 0, h->mx_V, m));      // G = V^H V
+    {
+      ProfScope ps(h, PK_REFINE, 0.0, 3.0 * (double)m * mp * sizeof(double2));
+      partition_correction_kernel<<<grid_for((size_t)(m - mp) * mp, h->num_sms), 256, 0, h->st>>>(
+          h->mx_G, h->mx_V, m, mp, h->mx_B);
+      CK(h, cudaGetLastError());
+    }
+    CK(h, mx_gemm(h, m, mp, m - mp, h->mx_W + mp, m, 0, h->mx_B, mp, 0, h->mx_W, m, 1.0, 1));   // V_P += V_R E
+  }
+  if (iterate) {
+    CK(h, mx_gemm(h, r, mp, m, h->mx_Q, m, 0, h->mx_W, m, 0, Qp, mp));
+  } else {
+    CK(h, cudaMemcpy2DAsync(Qp, (size_t)mp * sizeof(double2), h->mx_W, (size_t)m * sizeof(double2),
+                            (size_t)mp * sizeof(double2), r, cudaMemcpyDeviceToDevice, h->st));
+  }
+  rc = mx_newton_schulz(h, Qp, Qsp, r, mp, 3);
   if (rc) return rc;
-  if (steps > 0)
-    CK(h, cudaMemcpyAsync(h->mx_Q0, h->mx_Q, (size_t)r * m * sizeof(double2), cudaMemcpyDeviceToDevice, h->st));
-  // 3. subspace iteration in FP64, orthonormalising after each of the two
-  // products (W <- orth(X^H Q), Q <- orth(X W)), so that each basis has
-  // condition number sigma_1 / sigma_m rather than its square
-  for (int it = 0; it < steps; ++it) {
-    CK(h, mx_gemm(h, c, m, r, X, ldx, 1, h->mx_Q, m, 0, h->mx_T, m));     // T = X^H Q (c x m)
-    rc = mx_scholqr3(h, h->mx_T, h->mx_B, c, m);
-    if (rc) return rc;
-    CK(h, mx_gemm(h, r, m, c, X, ldx, 0, h->mx_T, m, 0, h->mx_Q2, m));    // X T (r x m)
-    std::swap(h->mx_Q, h->mx_Q2);
-    rc = mx_scholqr3(h, h->mx_Q, h->mx_Q2, r, m);
-    if (rc) return rc;
-  }
-  // 4. Rayleigh-Ritz on span(Q). The refined basis is first turned towards
-  // the FP32 singular vectors, Q <- Q W with W the orthonormal factor of
-  // G = Q^H Q0 (m x m; shifted CholeskyQR3 of G, so W is unitary to rounding
-  // whatever the conditioning of G), so that the rows of B = Q^H X start
-  // nearly orthogonal; then the FP64 one-sided (row) Jacobi SVD of B,
-  // B = U_B Lambda W^H, which keeps the small singular values' relative
-  // accuracy (no Gram matrix). Q U_B is the left factor.
-  if (steps > 0) {
-    double2 *Wm = h->mx_T, *Wspare = h->mx_B;                                // m x m in buffers of c x m
-    CK(h, mx_gemm(h, m, m, r, h->mx_Q, m, 1, h->mx_Q0, m, 0, Wm, m));         // G = Q^H Q0
-    rc = mx_scholqr3(h, Wm, Wspare, m, m);
-    if (rc) return rc;
-    CK(h, mx_gemm(h, r, m, m, h->mx_Q, m, 0, Wm, m, 0, h->mx_Q2, m));         // Q W
-    std::swap(h->mx_Q, h->mx_Q2);
-  }
-  CK(h, mx_gemm(h, m, c, r, h->mx_Q, m, 1, X, ldx, 0, h->mx_B, c));        // B = Q^H X
+  // 4. FP64 Rayleigh-Ritz (stage 2): B' = Q'^H X, H' = B' B'^H, nearly
+  // diagonal, and the FP64 Hermitian Jacobi eigen-solve H' = V diag(w) V^H
+  CK(h, mx_gemm(h, mp, c, r, Qp, mp, 1, X, ldx, 0, h->mx_B, c));            // B' (mp x c)
+  CK(h, mx_gemm(h, mp, mp, c, h->mx_B, c, 0, h->mx_B, c, 1, h->mx_G, mp));  // H' (mp x mp)
   {
-    ProfScope ps(h, PK_EIG64, 13.3 * (double)m * m * m, (2.0 * m * c + (double)m * m) * sizeof(double2));
-    CK(h, launch_onesided<double>(h->st, h->mx_B, m, c, c, h->mx_V, h->mx_w, h->mx_eosctl, h->opts.eig_max_sweeps,
-                                  h->opts.barrier_timeout_s, h->num_sms));
-  }
-  // left factor Q U_B, stored as rows conj(column j) = U_B^H Q^H with
-  // U_B^H = conj(U_B^T); the rows Lambda W^H of the rotated B go to X
-  {
-    ProfScope ps(h, PK_REFINE, 0.0, 2.0 * m * m * sizeof(double2));
-    conj_inplace_kernel<<<grid_for((size_t)m * m, h->num_sms), 256, 0, h->st>>>(h->mx_V, (size_t)m * m);
+    ProfScope ps(h, PK_EIG64, 13.3 * (double)mp * mp * mp, 3.0 * (double)mp * mp * sizeof(double2));
+    hermitise_kernel<<<grid_for((size_t)mp * mp, h->num_sms), 256, 0, h->st>>>(h->mx_G, mp);
     CK(h, cudaGetLastError());
+    CK(h, launch_jacobi<double>(h->st, h->mx_G, mp, h->mx_V, h->mx_w, &h->mx_eosctl->g, h->opts.eig_max_sweeps,
+                                h->opts.barrier_timeout_s, h->num_sms));
   }
-  CK(h, mx_gemm(h, m, r, m, h->mx_V, m, 0, h->mx_Q, m, 1, (double2*)h->vecs, r));
-  CK(h, cudaMemcpy2DAsync(X, (size_t)ldx * sizeof(double2), h->mx_B, (size_t)c * sizeof(double2),
-                          (size_t)c * sizeof(double2), m, cudaMemcpyDeviceToDevice, h->st));
+  // left factor Q' V, stored as rows conj(column j) = V^H Q'^H; the rows
+  // V^H B' = Lambda W^H go to X
+  CK(h, mx_gemm(h, mp, c, mp, h->mx_V, mp, 1, h->mx_B, c, 0, X, ldx));
+  CK(h, mx_gemm(h, mp, r, mp, h->mx_V, mp, 1, Qp, mp, 1, (double2*)h->vecs, r));
   h->vecs_conj = true;
   {
-    ProfScope ps(h, PK_SELECT, 0.0, (double)m * (sizeof(double) + sizeof(int) + sizeof(double)));
-    CK(h, launch_select<double>(h->st, h->mx_w, m, cap, h->cutoff * h->cutoff, h->perm, h->lam2, h->info,
-                                disc ? h->scal + 1 : nullptr, h->scal, S, sch, m < r ? h->scal + 2 : nullptr));
+    ProfScope ps(h, PK_SELECT, 0.0, (double)mp * (sizeof(double) + sizeof(int) + sizeof(double)));
+    CK(h, launch_select<double>(h->st, h->mx_w, mp, cap, h->cutoff * h->cutoff, h->perm, h->lam2, h->info,
+                                disc ? h->scal + 1 : nullptr, h->scal, S, sch, h->scal + 2));
   }
   CK(h, cudaMemcpyAsync(&h->hs->info, h->info, sizeof(SelectInfo), cudaMemcpyDeviceToHost, h->st));
   CK(h, cudaMemcpyAsync(&h->hs->ctl, &h->osctl->g, sizeof(GridCtl), cudaMemcpyDeviceToHost, h->st));
   CK(h, cudaMemcpyAsync(&h->hs->chol_status, h->mx_chst, sizeof(int), cudaMemcpyDeviceToHost, h->st));
   CK(h, cudaMemcpyAsync(h->hs->eig, &h->mx_eosctl->g, sizeof(GridCtl), cudaMemcpyDeviceToHost, h->st));
   if (h->use_oz) CK(h, cudaMemcpyAsync(&h->hs->oz_err, h->oz.status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
-  if (h->prof) CK(h, cudaMemcpyAsync(h->hs->phase_ns, h->osctl->phase_ns, sizeof(h->hs->phase_ns), cudaMemcpyDeviceToHost, h->st));
   CK(h, cudaStreamSynchronize(h->st));
-  if (h->prof) for (int i = 0; i < 3; ++i) h->prof_phase_ns[i] += h->hs->phase_ns[i];
-  if (h->hs->ctl.err) return fail(h, MPO_ERR_TIMEOUT, "grid barrier wait timed out in the FP32 SVD");
+  rc = msvd_status(h);
+  if (rc) return rc;
   h->last_sweeps = h->hs->ctl.sweeps;
   h->prof_sweeps += h->prof ? h->hs->ctl.sweeps : 0;
-  if (h->hs->ctl.status)
-    return fail(h, MPO_ERR_NOCONV, "FP32 Jacobi SVD reached eig_max_sweeps (" + std::to_string(r) + " x " + std::to_string(c) + ")");
-  if (h->use_oz && h->hs->oz_err) return fail(h, MPO_ERR_TIMEOUT, "an mbarrier wait timed out in the tensor-core FP64 GEMM");
-  if (h->hs->chol_status)
-    return fail(h, MPO_ERR_NOCONV, "Cholesky QR met a non-positive pivot (m = " + std::to_string(m) + ")");
-  if (h->hs->eig[0].err) return fail(h, MPO_ERR_TIMEOUT, "grid barrier wait timed out in the FP64 Rayleigh-Ritz SVD");
+  if (h->hs->eig[0].err) return fail(h, MPO_ERR_TIMEOUT, "grid barrier wait timed out in the FP64 Rayleigh-Ritz eigen-solve");
   if (h->hs->eig[0].status)
-    return fail(h, MPO_ERR_NOCONV, "FP64 Rayleigh-Ritz SVD reached eig_max_sweeps (m = " + std::to_string(m) + ")");
-
+    return fail(h, MPO_ERR_NOCONV, "FP64 Rayleigh-Ritz eigen-solve reached eig_max_sweeps (m = " + std::to_string(mp) + ")");
   *k = h->hs->info.k;
   return MPO_OK;
 }
@@ -740,8 +815,80 @@ static cudaError_t conj_transpose(mpo_ctx* h, const cplx<T>* in, int r, int c, i
 // Centre at site k -> site k becomes a left isometry, centre moves to k+1.
 // L(C) = Y^H with Y = U X' (one-sided SVD of Y): Q = X'^H Sigma^-1 -> site k,
 // R = Sigma U^H / ||kept|| pushed into site k+1.
+// Precision form, centre moves that record nothing: the centre C becomes an
+// isometry by Cholesky QR instead of an SVD (the move needs a basis of the
+// bond space, not its Schmidt decomposition; the state C = Q (Q^H C) is
+// unchanged up to rounding). Y (rows x r) is orthonormalised by
+// kMovePasses mixed-precision Cholesky QR passes, which take a condition
+// number up to ~1e7 (the cutoff's 1e-7 floor on the bond weights) to about
+// 1, and three Newton-Schulz steps to FP64 orthonormality. The orthonormality
+// defect entering the last Newton-Schulz step (its Gram matrix) is read back:
+// above 1e-5 the move falls back to the SVD route and returns 1.
+constexpr int kMovePasses = 5;
+
+static int mx_isometry(mpo_ctx* h, double2*& Y, int rows, int r, bool* ok) {
+  double2* sp = h->mx_Q2;
+  CK(h, cudaMemsetAsync(h->mx_chst, 0, sizeof(int), h->st));
+  int rc = mx_cholqr(h, Y, sp, rows, r, kMovePasses);
+  if (rc) return rc;
+  rc = mx_newton_schulz(h, Y, sp, rows, r, 2);
+  if (rc) return rc;
+  CK(h, mx_gemm(h, r, r, rows, Y, r, 1, Y, r, 0, h->mx_G, r));
+  defect_kernel<<<1, 1024, 0, h->st>>>(h->mx_G, r, h->scal + 3);
+  CK(h, cudaGetLastError());
+  rc = mx_newton_schulz(h, Y, sp, rows, r, 1);
+  if (rc) return rc;
+  double defect = 1.0;
+  CK(h, cudaMemcpyAsync(&defect, h->scal + 3, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(h, cudaMemcpyAsync(&h->hs->chol_status, h->mx_chst, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  if (h->use_oz) CK(h, cudaMemcpyAsync(&h->hs->oz_err, h->oz.status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(h, cudaStreamSynchronize(h->st));
+  if (h->use_oz && h->hs->oz_err) return fail(h, MPO_ERR_TIMEOUT, "an mbarrier wait timed out in the tensor-core FP64 GEMM");
+  *ok = !h->hs->chol_status && defect <= 1e-5;
+  return MPO_OK;
+}
+
+static int mx_move_right(mpo_ctx* h, int k, bool* done) {
+  const int mX = 4 * h->chi[k], r = h->chi[k + 1], mR = 4 * h->chi[k + 2];
+  double2* C = (double2*)h->site[k];                                          // mX x r
+  double2* Y = h->mx_Q;
+  CK(h, cudaMemcpyAsync(Y, C, (size_t)mX * r * sizeof(double2), cudaMemcpyDeviceToDevice, h->st));
+  int rc = mx_isometry(h, Y, mX, r, done);
+  if (rc || !*done) return rc;
+  CK(h, mx_gemm(h, r, r, mX, Y, r, 1, C, r, 0, h->mx_W, r));                 // R = Q^H C
+  CK(h, mx_gemm(h, r, mR, r, h->mx_W, r, 0, (const double2*)h->site[k + 1], mR, 0, (double2*)h->spare, mR));
+  swap_spare(h, k + 1);
+  CK(h, cudaMemcpyAsync(h->spare, Y, (size_t)mX * r * sizeof(double2), cudaMemcpyDeviceToDevice, h->st));
+  swap_spare(h, k);
+  h->centre = k + 1;
+  return MPO_OK;
+}
+
+static int mx_move_left(mpo_ctx* h, int k, bool* done) {
+  const int r = h->chi[k], mR = 4 * h->chi[k + 1], mL = 4 * h->chi[k - 1];
+  double2* C = (double2*)h->site[k];                                          // r x mR
+  double2* Y = h->mx_Q;
+  CK(h, conj_transpose<double>(h, C, r, mR, mR, Y, r));                       // C^H (mR x r)
+  int rc = mx_isometry(h, Y, mR, r, done);
+  if (rc || !*done) return rc;
+  CK(h, mx_gemm(h, r, r, mR, C, mR, 0, Y, r, 0, h->mx_W, r));                // L = C Q
+  CK(h, mx_gemm(h, mL, r, r, (const double2*)h->site[k - 1], r, 0, h->mx_W, r, 0, (double2*)h->spare, r));
+  swap_spare(h, k - 1);
+  CK(h, conj_transpose<double>(h, Y, mR, r, r, (double2*)h->spare, mR));     // Q^H (r x mR)
+  swap_spare(h, k);
+  h->centre = k - 1;
+  return MPO_OK;
+}
+
 template <typename T>
 static int move_right(mpo_ctx* h, int k) {
+  if constexpr (std::is_same<T, double>::value) {
+    if (h->mixed) {
+      bool done = false;
+      int rc0 = mx_move_right(h, k, &done);
+      if (rc0 || done) return rc0;
+    }
+  }
   const int mX = 4 * h->chi[k], r = h->chi[k + 1], mR = 4 * h->chi[k + 2];
   cplx<T>* Y = (cplx<T>*)h->theta2;
   cplx<T>* tmp = (cplx<T>*)h->tmp;
@@ -765,6 +912,13 @@ static int move_right(mpo_ctx* h, int k) {
 // Schmidt values of bond k; with record they and the entropy are stored.
 template <typename T>
 static int move_left(mpo_ctx* h, int k, bool record) {
+  if constexpr (std::is_same<T, double>::value) {
+    if (h->mixed && !record) {
+      bool done = false;
+      int rc0 = mx_move_left(h, k, &done);
+      if (rc0 || done) return rc0;
+    }
+  }
   const int r = h->chi[k], mR = 4 * h->chi[k + 1], mL = 4 * h->chi[k - 1];
   cplx<T>* Y = S_<T>(h, k);
   cplx<T>* tmp = (cplx<T>*)h->tmp;
@@ -1059,11 +1213,15 @@ static bool alloc_factor_ws(mpo_ctx* h, int m, int ccap, size_t bj_nch) {
     ok = ok && alloc((void**)&h->mx_V, mm * mm * sizeof(double2));
     ok = ok && alloc((void**)&h->mx_G, mm * mm * sizeof(double2));
     ok = ok && alloc((void**)&h->mx_w, mm * sizeof(double));
-    ok = ok && alloc((void**)&h->mx_Li, mm * mm * sizeof(double2));
+    ok = ok && alloc((void**)&h->mx_W, mm * mm * sizeof(double2));
     ok = ok && alloc((void**)&h->mx_eosctl, sizeof(OSCtl));
     ok = ok && alloc((void**)&h->mx_Q0, (size_t)m * mm * sizeof(double2));
-    ok = ok && alloc((void**)&h->mx_ptmp, mm * mm * sizeof(double2));
+    ok = ok && alloc((void**)&h->mx_A32, mm * mm * sizeof(float2));
+    ok = ok && alloc((void**)&h->mx_Li32, mm * mm * sizeof(float2));
+    ok = ok && alloc((void**)&h->mx_t32, mm * mm * sizeof(float2));
+    ok = ok && alloc((void**)&h->mx_d, mm * sizeof(double));
     ok = ok && alloc((void**)&h->mx_chst, sizeof(int));
+    if (ok) ok = ensure_dynamic_smem((const void*)chol_diag_kernel<float, CHOL32_NB>, chol_smem_bytes<float, CHOL32_NB>()) == cudaSuccess;
   }
   return ok;
 }
@@ -1120,9 +1278,10 @@ int mpo_init(mpo_handle* out, int n, int chi_max, mpo_precision prec, void* stre
   h->tensor_cores = prec == MPO_FP32 && h->opts.tensor_cores > 0;
   h->block_min_rows = h->opts.block_jacobi_min_rows < 0 ? 0
                       : (h->opts.block_jacobi_min_rows > 0 ? h->opts.block_jacobi_min_rows : (prec != MPO_FP64 ? 64 : 0));
-  // precision form: FP32 approximate SVD with oversampling, FP64 refinement
+  // precision form: subspace iteration on chi_max + oversample directions,
+  // FP32 and FP64 Rayleigh-Ritz steps
   h->mx_over = h->opts.oversample > 0 ? h->opts.oversample : (h->opts.oversample < 0 ? 0 : chi_max);
-  h->mx_steps = h->opts.refine_steps > 0 ? std::min(h->opts.refine_steps, 7) : (h->opts.refine_steps < 0 ? 0 : 5);
+  h->mx_steps = h->opts.refine_steps > 0 ? std::min(h->opts.refine_steps, kMixedMaxSteps) : (h->opts.refine_steps < 0 ? 1 : kMixedSteps);
   h->mx_mcap = std::min(m, chi_max + h->mx_over);
   // FP64-accurate products on the tensor cores (BF16 slices) unless switched off
   h->use_oz = h->mixed && h->opts.tensor_cores >= 0;
@@ -1140,7 +1299,8 @@ int mpo_init(mpo_handle* out, int n, int chi_max, mpo_precision prec, void* stre
                                       2 * (size_t)m * h->mx_mcap * sizeof(double2) +
                                       2 * (size_t)mx_ccap * h->mx_mcap * sizeof(double2) +
                                       2 * (size_t)h->mx_mcap * h->mx_mcap * sizeof(double2) +
-                                      4 * (size_t)h->mx_mcap * h->mx_mcap * sizeof(double2) +
+                                      2 * (size_t)h->mx_mcap * h->mx_mcap * sizeof(double2) +
+                                      3 * (size_t)h->mx_mcap * h->mx_mcap * sizeof(float2) +
                                       (size_t)m * h->mx_mcap * sizeof(double2) + (size_t)h->mx_mcap * sizeof(double)
                                 : 0) +
                       (h->use_oz ? (size_t)oz::S * 2 * 3 * (size_t)std::max(m, mx_ccap) * 2 *
@@ -1214,7 +1374,7 @@ void mpo_free(mpo_handle h) {
                 h->dsup, h->dp, h->info, h->ctl, h->scal, h->dS, h->dschmidt, h->tv0, h->tv1,
                 h->mx_a32, h->mx_ut32, h->mx_w32, h->mx_perm32, h->mx_lam32, h->mx_info32, h->mx_Q, h->mx_Q2,
                 h->mx_B, h->mx_T, h->mx_V, h->mx_G, h->mx_w,
-                h->mx_Li, h->mx_ptmp, h->mx_chst, h->mx_eosctl, h->mx_Q0};
+                h->mx_W, h->mx_A32, h->mx_Li32, h->mx_t32, h->mx_d, h->mx_chst, h->mx_eosctl, h->mx_Q0};
   for (void* p : ps) if (p) cudaFree(p);
   if (h->hs) cudaFreeHost(h->hs);
   free_oz(h->oz);
@@ -1514,7 +1674,7 @@ int mpo_svd_truncated(int r, int c, const void* A, int cap, mpo_precision prec, 
   h->block_min_rows = h->opts.block_jacobi_min_rows < 0 ? 0
                       : (h->opts.block_jacobi_min_rows > 0 ? h->opts.block_jacobi_min_rows : (prec != MPO_FP64 ? 64 : 0));
   h->mx_over = h->opts.oversample > 0 ? h->opts.oversample : (h->opts.oversample < 0 ? 0 : cap);
-  h->mx_steps = h->opts.refine_steps > 0 ? std::min(h->opts.refine_steps, 7) : (h->opts.refine_steps < 0 ? 0 : 5);
+  h->mx_steps = h->opts.refine_steps > 0 ? std::min(h->opts.refine_steps, kMixedMaxSteps) : (h->opts.refine_steps < 0 ? 1 : kMixedSteps);
   h->mx_mcap = std::min(r, cap + h->mx_over);
   h->use_oz = h->mixed && h->opts.tensor_cores >= 0;
   const size_t nch = (size_t)(c + JCW - 1) / JCW + 1;
@@ -1527,6 +1687,7 @@ int mpo_svd_truncated(int r, int c, const void* A, int cap, mpo_precision prec, 
   auto ck = [&](cudaError_t e) { if (rc == MPO_OK && e != cudaSuccess) { rc = MPO_ERR_CUDA; g_last_init_error = cudaGetErrorString(e); } };
   ck(cudaMemcpyAsync(h->theta, A, (size_t)r * c * h->esz, cudaMemcpyDeviceToDevice, h->st));
   ck(cudaMemsetAsync(h->scal, 0, 4 * sizeof(double), h->st));
+  ck(cudaMemsetAsync(h->tc_status, 0, sizeof(int), h->st));
   if (rc == MPO_OK) {
     rc = prec != MPO_FP32 ? svd_select<double>(h, (double2*)h->theta, r, c, c, cap, true, nullptr, nullptr, &kk)
                           : svd_select<float>(h, (float2*)h->theta, r, c, c, cap, true, nullptr, nullptr, &kk);
