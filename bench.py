@@ -2,23 +2,24 @@
 """Throughput of the GB300 noisy-MPO engine on the paper's workload.
 
 Metric: noisy-gate MPO updates per second at chi_max = 1024 (n = 64 qubits,
-Haar brickwork, two-qubit depolarising p = 0.005, seed 2). One timed step is
-one brickwork layer (time step of Sec. 2.1): its n/2 or n/2-1 noisy gates,
-each contraction + superoperator + truncated SVD + write-back, then the
-end-of-step Schmidt sweep and entropy at every bond. Before timing, the
-circuit is run until every bond sits at its cap (ramp layers, untimed), then W
-warm-up layers.
+Haar brickwork, two-qubit depolarising p = 0.005, seed 2) in the precision
+form, with its accuracy against the FP64 form. One timed step is one noisy
+gate (the unit of the hot-path scope): the centre move onto its bond, the
+contraction, superoperator, truncated SVD and write-back; the end-of-step
+Schmidt sweep and entropy run with the last gate of each brickwork step.
+Before timing, ramp layers run until the bonds reach their cap, then W
+warm-up gates.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
-                    [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64|mixed]
+                    [--workload NAME] [--impl reference]
 
 Prints one JSON line. ``value`` is gates/s with gates already resident in HBM;
-``e2e`` is the same metric through the C ABI with host gate buffers (H2D
-copies inside the timed region) and the entropies read back every step.
-Under torchrun each rank simulates an independent circuit (seed + rank):
-a single circuit does not shard, so N GPUs run N replicas (weak scaling).
-``--impl reference`` times the CPU oracle instead (test infrastructure, the
-only other code path here that may run it).
+``e2e`` is the same metric through the C ABI with pinned host gate buffers
+(H2D copies inside the timed region) and the entropies read back at the end
+of every brickwork step. Under torchrun each rank simulates an independent
+circuit (seed + rank): a single circuit does not shard, so N GPUs run N
+replicas (weak scaling). ``--impl reference`` times the CPU oracle instead
+(test infrastructure, the only other code path here that may run it).
 """
 from __future__ import annotations
 
@@ -39,15 +40,15 @@ sys.path.insert(0, ROOT)
 
 WORKLOADS = {
     # n, chi_max, p, seed, default precision
-    "n64_chi1024_p0.005": dict(n=64, chi=1024, p=0.005, seed=2, precision="fp32"),
-    "n32_chi256_p0.01": dict(n=32, chi=256, p=0.01, seed=1, precision="fp64"),
+    "n64_chi1024_p0.005": dict(n=64, chi=1024, p=0.005, seed=2, precision="mixed", centre_only=True),
+    "n32_chi256_p0.01": dict(n=32, chi=256, p=0.01, seed=1, precision="fp64", centre_only=True),
     "n8_chi256_p0.02": dict(n=8, chi=256, p=0.02, seed=0, precision="fp64"),
     # batching form: 256 instances, n_i in {16, 24, ..., 64}, p_i in {.005, .01,
     # .02, .05} from PCG64(4), D_i = 2 n_i, instance gates from PCG64(1000 + i)
     "batch256_chi128": dict(n=64, chi=128, p=0.02, seed=4, precision="fp32", batch=256),
 }
 DEFAULT_WORKLOAD = "n64_chi1024_p0.005"
-METRIC = "noisy-gate MPO updates/s at chi=1024 (n=64 Haar brickwork, p=0.005)"
+METRIC = "noisy-gate MPO updates/s at chi=1024 (mixed vs FP64, |dS|<=1e-6); % roofline"
 
 # FP64 and FP32 SIMT rates measured on this GPU model with an FMA-chain probe
 # (8 independent chains per thread, 152 x 8 CTAs of 256 threads, CUDA events):
@@ -71,33 +72,38 @@ def load_peaks() -> dict:
             "fp32_simt_tflops": FP32_PROBE_TFLOPS, "source": src}
 
 
-def step_work(dims, n: int, parity: int, chi: int, prec: str, over: int, centre_only: bool) -> dict:
-    """Algorithmic work of one brickwork step as the hot-path scope counts it
-    (real flops, complex multiply-add = 8), from the bond dimensions dims:
-    per gate theta 8 (4 chiL)(4 chiR) chiM, superoperator 2048 chiL chiR,
-    Hermitian Gram of theta' 4 r^2 c, projection to the kept right factor
-    8 k r c (r, c = the shorter and longer side of theta', k = min(chi, r)),
-    and the Hermitian eigen-solve 13.3 m^3 with m = min(r, chi + oversample)
-    (precision form) or m = r; per recorded bond of the Schmidt sweep a
-    chi_b x 4 chi_{b+1} factorisation, 12 r^2 c GEMM-class + 13.3 r^3. Bytes:
-    the four site tensors each gate reads or writes."""
+MIXED_MARGIN = 64        # Ritz directions beyond chi_max in the precision form's FP64 step
+
+
+def gate_work(dims, i: int, chi: int, prec: str) -> dict:
+    """Algorithmic work of one noisy gate on sites (i, i+1) as the hot-path
+    scope counts it (real flops, complex multiply-add = 8), from the bond
+    dimensions dims: theta 8 (4 chiL)(4 chiR) chiM, superoperator
+    2048 chiL chiR, Hermitian Gram of theta' 4 r^2 c, projection onto the kept
+    right factor 8 k r c (r, c = the shorter and longer side of theta',
+    k = min(chi, r)), the centre move onto the bond (a 4 chiM x chiM
+    factorisation, 12 chiM^2 (4 chiM)); the Hermitian eigen-solve 13.3 m^3,
+    m = min(r, chi + 64) in the precision form, r otherwise. Bytes: the site
+    tensors the gate reads and writes."""
     esz = 8 if prec == "fp32" else 16
-    gemm = solve = byts = 0.0
-    for l in range(1 + parity, n, 2):
-        i = l - 1
-        cl, cm, cr = dims[i], dims[i + 1], dims[i + 2]
-        r, c = 4 * min(cl, cr), 4 * max(cl, cr)
-        k = min(chi, r)
-        gemm += 8.0 * (4 * cl) * (4 * cr) * cm + 2048.0 * cl * cr + 4.0 * r * r * c + 8.0 * k * r * c
-        m = min(r, chi + over) if prec == "mixed" else r
-        solve += 13.3 * m ** 3
-        byts += 2.0 * (cl * 4 * cm + cm * 4 * cr) * esz
-    bonds = [n // 2] if centre_only else range(1, n)
-    for b in bonds:
+    cl, cm, cr = dims[i], dims[i + 1], dims[i + 2]
+    r, c = 4 * min(cl, cr), 4 * max(cl, cr)
+    k = min(chi, r)
+    gemm = 8.0 * (4 * cl) * (4 * cr) * cm + 2048.0 * cl * cr + 4.0 * r * r * c + 8.0 * k * r * c
+    gemm += 12.0 * cm * cm * (4 * cm)
+    m = min(r, chi + MIXED_MARGIN) if prec == "mixed" else r
+    return {"gemm": gemm, "solve": 13.3 * m ** 3, "bytes": 2.0 * (cl * 4 * cm + cm * 4 * cr) * esz}
+
+
+def sweep_work(dims, n: int, centre_only: bool) -> dict:
+    """The end-of-step Schmidt sweep: per recorded bond b a chi_b x 4 chi_{b+1}
+    factorisation, 12 r^2 c GEMM-class + 13.3 r^3 solve."""
+    gemm = solve = 0.0
+    for b in ([n // 2] if centre_only else range(1, n)):
         r, c = dims[b], 4 * dims[b + 1]
         gemm += 12.0 * r * r * c
         solve += 13.3 * r ** 3
-    return {"gemm": gemm, "solve": solve, "bytes": byts}
+    return {"gemm": gemm, "solve": solve, "bytes": 0.0}
 
 
 def ramp_layers(n: int, chi: int) -> int:
@@ -312,27 +318,66 @@ def run_batch(args, wl, prec) -> None:
         dist.destroy_process_group()
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default=None, choices=["fp32", "fp64", "mixed"])
-    ap.add_argument("--centre-only", action="store_true", help="record S at the centre bond only")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workers", type=int, default=8, help="host worker threads of the batching form")
-    args = ap.parse_args()
-    wl = WORKLOADS[args.workload]
-    if args.impl == "reference":
-        run_reference(args, wl)
-        return
-    prec = args.precision or wl["precision"]
-    if "batch" in wl:
-        run_batch(args, wl, prec)
-        return
+def gate_schedule(circ, n: int, t_first: int, count: int):
+    """(time step, gate index, ABI bond, last gate of its step) for `count`
+    consecutive gates from the first gate of step t_first."""
+    out = []
+    t = t_first
+    while len(out) < count:
+        par = circ.parity(t)
+        ng = len(circ.gates[t - 1])
+        for g in range(ng):
+            out.append((t, g, 2 * g + par, g == ng - 1))
+            if len(out) == count:
+                break
+        t += 1
+    return out
 
+
+def accuracy_checks(mpo_mod, m, circ, sched_next, chi: int) -> dict:
+    """Accuracy of the precision form against the FP64 form, outside the
+    timed regions: (1) |dS| at every bond after every step of a 12-step
+    n = 16, chi = 64, p = 0.005 trajectory (seed 0) run through both forms;
+    (2) the kept-theta relative Frobenius error of the next gate of the
+    benchmark circuit itself (chi = 1024): its theta' (mpo_theta) truncated by
+    both forms' SVDs (mpo_svd_truncated), compared."""
+    import torch
+    from paper_2003_13163_gb300.circuits import random_circuit
+    out = {}
+    c16 = random_circuit(16, 12, 0.005, seed=0)
+    S = {}
+    for prec in ("fp64", "mixed"):
+        q = mpo_mod.MPO(16, 64, prec)
+        rows = []
+        for t in range(1, 13):
+            q.apply_layer(c16.parity(t), c16.gates[t - 1], c16.p[t - 1])
+            rows.append(q.entropy(with_trace=False)[0])
+        q.close()
+        S[prec] = np.array(rows)
+    out["dS_max_n16_chi64_12steps"] = float(np.abs(S["mixed"] - S["fp64"]).max())
+    t, g, b, _ = sched_next
+    At = m.theta(b, circ.gates[t - 1][g], float(circ.p[t - 1][g]))   # theta' of the next gate, untruncated
+    if At.shape[0] > At.shape[1]:
+        At = At.conj().T.contiguous()
+    At = At / torch.linalg.norm(At)
+    t0 = time.perf_counter()
+    U64, X64, _ = mpo_mod.svd_truncated(At, chi, "fp64", cutoff=1e-12)
+    t64 = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Um, Xm, _ = mpo_mod.svd_truncated(At, chi, "mixed")
+    torch.cuda.synchronize()
+    tm = time.perf_counter() - t0
+    ref = U64 @ X64
+    err = float(torch.linalg.norm(Um @ Xm - ref) / torch.linalg.norm(ref))
+    out.update({"kept_theta_rel_err_chi1024": err, "theta_shape": list(At.shape),
+                "fp64_svd_seconds": round(t64, 2), "mixed_svd_seconds": round(tm, 2)})
+    return out
+
+
+def run_single(args, wl, prec) -> None:
+    """One circuit per rank; a timed step is one noisy gate (a2-a6 on its
+    bond), the end-of-step sweep and entropy charged to the step's last gate."""
     import torch
     from paper_2003_13163_gb300 import replicas
     world, rank, local = replicas.world()
@@ -350,32 +395,42 @@ def main():
     from paper_2003_13163_gb300.circuits import random_circuit
 
     n, chi, p = wl["n"], wl["chi"], wl["p"]
+    centre_only = args.centre_only or wl.get("centre_only", False)
     R = ramp_layers(n, chi)
     K, W = args.steps, args.warmup
-    depth = R + W + 2 * K
+    per_layer = n // 2 - 0.5
+    depth = R + int(math.ceil((W + 2 * K + 1) / per_layer)) + 2
     circ = random_circuit(n, depth, p, replicas.rank_seed(wl["seed"], rank))
+    sched = gate_schedule(circ, n, R + 1, W + 2 * K + 1)
     # device-resident gates for the kernel-only number, pinned host copies for e2e
-    dg = [torch.from_numpy(g.view(np.float64).copy()).to(dev) for g in circ.gates]
-    dpv = [torch.from_numpy(pp.copy()).to(dev) for pp in circ.p]
-    hg = [torch.from_numpy(g.view(np.float64).copy()).pin_memory() for g in circ.gates]
-    hp = [torch.from_numpy(pp.copy()).pin_memory() for pp in circ.p]
+    dg = {(t, g): torch.from_numpy(circ.gates[t - 1][g].view(np.float64).copy()).to(dev) for t, g, _, _ in sched}
+    hg = {(t, g): torch.from_numpy(circ.gates[t - 1][g].view(np.float64).copy()).pin_memory()
+          for t, g, _, _ in sched}
 
     stream = torch.cuda.current_stream(dev)
-    m = mpo.MPO(n, chi, prec, stream=stream.cuda_stream, centre_only=args.centre_only)
-    t = 0
-
-    def layer_dev(tt):
-        m.apply_layer(circ.parity(tt), dg[tt - 1], dpv[tt - 1])
+    m = mpo.MPO(n, chi, prec, stream=stream.cuda_stream, centre_only=centre_only)
 
     t_ramp0 = time.perf_counter()
-    for _ in range(R):
-        t += 1
-        layer_dev(t)
+    for t in range(1, R + 1):
+        m.apply_layer(circ.parity(t), circ.gates[t - 1], circ.p[t - 1])
     torch.cuda.synchronize()
     t_ramp = time.perf_counter() - t_ramp0
+
+    def step(entry, bufs, read_back):
+        t, g, b, last = entry
+        m.apply_gate(b, bufs[(t, g)], float(circ.p[t - 1][g]))
+        d2h = 0
+        if last:
+            m.sweep()
+            if read_back:
+                S, _, _ = m.entropy(with_trace=False)
+                d2h = S.nbytes
+        return d2h
+
+    pos = 0
     for _ in range(W):
-        t += 1
-        layer_dev(t)
+        step(sched[pos], dg, False)
+        pos += 1
     torch.cuda.synchronize()
     dims = m.bond_dims()
 
@@ -385,51 +440,50 @@ def main():
         return replicas.max_over_ranks(x, device=dev)
 
     # ---- kernel-only timed region: gates resident in HBM --------------------
-    gates_timed = 0
     clocks = ClockSampler(torch.cuda.current_device())
     barrier()
     torch.cuda.synchronize()
     clocks.start()
     m.profile(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    timed = sched[pos:pos + K]
     e0.record(stream)
-    for _ in range(K):
-        t += 1
-        gates_timed += len(circ.gates[t - 1])
-        layer_dev(t)
+    for entry in timed:
+        step(entry, dg, False)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
+    pos += K
     ms = e0.elapsed_time(e1)
     prof = m.profile_read()
     m.profile(False)
     clk = clocks.stop()
     ms_max = max_over_ranks(ms)
-    gates_all = gates_timed * world
-    value = gates_all / (ms_max / 1e3)
+    value = K * world / (ms_max / 1e3)
+    work = {"gemm": 0.0, "solve": 0.0, "bytes": 0.0}
+    for t, g, b, last in timed:
+        for key, v in gate_work(dims, b, chi, prec).items():
+            work[key] += v
+        if last:
+            for key, v in sweep_work(dims, n, centre_only).items():
+                work[key] += v
 
     # ---- end-to-end through the C ABI with host buffers ----------------------
     barrier()
     torch.cuda.synchronize()
     h2d = d2h = 0
-    gates_e2e = 0
-    w0 = time.perf_counter()
     e2 = torch.cuda.Event(enable_timing=True)
     e3 = torch.cuda.Event(enable_timing=True)
     e2.record(stream)
-    for _ in range(K):
-        t += 1
-        g, pp = hg[t - 1], hp[t - 1]
-        m.apply_layer(circ.parity(t), g, pp)
-        S, _, _ = m.entropy(with_trace=False)
-        gates_e2e += len(circ.gates[t - 1])
-        h2d += g.numel() * 8 + pp.numel() * 8
-        d2h += S.nbytes + 8
+    for entry in sched[pos:pos + K]:
+        d2h += step(entry, hg, True)
+        h2d += 32 * 8 + 8
     e3.record(stream)
     torch.cuda.synchronize()
     barrier()
+    pos += K
     e2e_ms = max_over_ranks(e2.elapsed_time(e3))
-    e2e_value = gates_e2e * world / (e2e_ms / 1e3)
+    e2e_value = K * world / (e2e_ms / 1e3)
     S, tr, dw = m.entropy()
 
     # ---- rooflines -----------------------------------------------------------
@@ -442,12 +496,20 @@ def main():
     classes = {k: v for k, v in prof.items() if not k.startswith("_") and v["launches"] > 0}
     dom = max(classes, key=lambda k: classes[k]["ms"])
     d = classes[dom]
-    fp64_classes = {"refine_gemm", "eig_fp64"} | ({"svd_gate", "svd_sweep", "cgemm"} if prec != "fp32" else set())
-    if prec == "mixed":
-        fp64_classes -= {"svd_gate", "svd_sweep"}      # the FP32 Jacobi SVD of the precision form
-    tensor_classes = {"svd_gate", "svd_sweep", "cgemm", "tc_cgemm"} - fp64_classes
-    if dom in fp64_classes:
+    fp64_classes = {"refine_gemm", "eig_fp64"} | ({"svd_gate", "svd_sweep", "cgemm"} if prec == "fp64" else set())
+    tensor_classes = {"cgemm", "tc_cgemm"} if prec != "fp64" else set()
+    if dom == "oz_gemm":
+        bound, unit = "tensor", "TFLOP/s"
+        pk = peaks["bf16_tflops"] / 21.0
+        basis = (f"BF16 tensor sustained ({peaks['source']}) / 21: the split scheme's BF16 products per "
+                 "FP64-accurate product (6 slices, levels 2..7)")
+        achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
+    elif dom in fp64_classes:
         bound, pk, unit, basis = "alu", peaks["fp64_tflops"], "TFLOP/s", "FP64 FMA probe 1.20 TFLOP/s"
+        achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
+    elif dom in ("svd_gate", "svd_sweep"):
+        bound, pk, unit = "alu", peaks["fp32_simt_tflops"], "TFLOP/s"
+        basis = "FP32 FMA probe 74.6 TFLOP/s (the one-sided Jacobi runs on the FP32 pipes)"
         achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
     elif dom in tensor_classes:
         bound, pk, unit = "tensor", peaks["tf32_tflops"], "TFLOP/s"
@@ -459,32 +521,29 @@ def main():
     roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": pk, "unit": unit,
                 "frac": achieved / pk, "traffic": None, "peak_basis": basis,
                 "share_of_step": d["ms"] / ms, "launches": d["launches"], "avg_launch_ms": d["ms"] / d["launches"]}
-    over = chi if prec == "mixed" else 0
-    w = {"gemm": 0.0, "solve": 0.0, "bytes": 0.0}
-    for tt in range(t - 2 * K + 1, t - K + 1):          # the timed steps
-        sw = step_work(dims, n, circ.parity(tt), chi, prec, over, args.centre_only)
-        for key in w:
-            w[key] += sw[key]
     p_gemm = peaks["fp64_tflops"] if prec == "fp64" else peaks["tf32_tflops"]
     p_solve = peaks["fp32_simt_tflops"] if prec == "fp32" else peaks["fp64_tflops"]
-    t_roof = w["gemm"] / (p_gemm * 1e12) + w["solve"] / (p_solve * 1e12) + w["bytes"] / (peaks["hbm_gbs"] * 1e9)
+    t_roof = work["gemm"] / (p_gemm * 1e12) + work["solve"] / (p_solve * 1e12) + work["bytes"] / (peaks["hbm_gbs"] * 1e9)
     step_roofline = {"t_roof_ms_per_step": 1e3 * t_roof / K, "measured_ms_per_step": ms / K,
-                     "frac": t_roof / (ms / 1e3), "gemm_flops_per_step": w["gemm"] / K,
-                     "solve_flops_per_step": w["solve"] / K, "bytes_per_step": w["bytes"] / K,
+                     "frac": t_roof / (ms / 1e3), "gemm_flops_per_step": work["gemm"] / K,
+                     "solve_flops_per_step": work["solve"] / K, "bytes_per_step": work["bytes"] / K,
                      "p_gemm_tflops": p_gemm, "p_solve_tflops": p_solve, "hbm_gbs": peaks["hbm_gbs"],
                      "peaks": peaks["source"]}
     kernels = {k: {"ms": round(v["ms"], 3), "launches": v["launches"], "share": round(v["ms"] / ms, 4),
                    "flops": v["flops"], "bytes": v["bytes"]}
                for k, v in classes.items()}
-
+    layers_timed = sum(1 for e in timed if e[3])
     line = {"metric": METRIC, "value": value, "unit": "gates/s", "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "fp64": "f64", "mixed": "f32+f64"}[prec], "data": "synthetic",
+            "dtype": {"fp32": "f32", "fp64": "f64", "mixed": "f64 (FP32 solves + split-BF16 products)"}[prec],
+            "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "chi_max": chi, "p": p, "seed": wl["seed"],
-                       "precision": prec, "entropy": "centre bond" if args.centre_only else "every bond",
-                       "oversample": over, "parallelism": f"replicas{world}", "ramp_layers": R,
-                       "ramp_seconds": round(t_ramp, 2), "gates_per_step": gates_timed / K,
-                       "max_bond_dim": int(max(dims)), "l2": "inputs larger than L2 (site tensors "
+                       "precision": prec, "step": "one noisy gate (a2-a6); the end-of-step sweep and entropy "
+                       "with the step's last gate", "entropy": "centre bond" if centre_only else "every bond",
+                       "parallelism": f"replicas{world}", "ramp_layers": R, "ramp_seconds": round(t_ramp, 2),
+                       "warmup_gates": W, "timed_gates": K, "layer_ends_timed": layers_timed,
+                       "max_bond_dim": int(max(dims)), "bond_dims_min_centre": int(min(dims[n // 4: 3 * n // 4])),
+                       "l2": "inputs larger than L2 (site tensors "
                        f"{m.device_bytes() / 2**30:.1f} GiB)", "final_S_centre": float(S[n // 2 - 1]),
                        "final_trace": tr},
             "clocks": clk,
@@ -492,11 +551,12 @@ def main():
             "roofline": roofline,
             "step_roofline": step_roofline,
             "kernels": kernels,
-            "svd_sweeps_per_launch": prof["_sweeps"] / max(1, sum(prof.get(k, {}).get("launches", 0)
-                                                                    for k in ("svd_gate", "svd_sweep"))),
-            "block_jacobi_phase_ms": {k: round(v, 1) for k, v in prof["_block_jacobi_phase_ms"].items()},
+            "subspace_steps_per_gate": prof.get("_steps", 0) / K,
+            "svd_sweeps_total": prof["_sweeps"],
             "e2e": {"value": e2e_value, "unit": "gates/s", "h2d_bytes_per_step": h2d // K,
                     "d2h_bytes_per_step": d2h // K}}
+    if prec == "mixed" and rank == 0 and not args.no_accuracy:
+        line["accuracy_vs_fp64"] = accuracy_checks(mpo, m, circ, sched[pos], chi)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         smp = oracle_gate_sample(chi, p, wl["seed"])
         line["cpu_baseline"] = {"value": 1.0 / smp["seconds_per_gate"], "unit": "gates/s", "cores": cpu_threads(),
@@ -509,6 +569,31 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default=None, choices=["fp32", "fp64", "mixed"])
+    ap.add_argument("--centre-only", action="store_true", help="record S at the centre bond only")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the precision form's FP64 comparisons")
+    ap.add_argument("--workers", type=int, default=8, help="host worker threads of the batching form")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+        return
+    prec = args.precision or wl["precision"]
+    if "batch" in wl:
+        run_batch(args, wl, prec)
+        return
+
+    run_single(args, wl, prec)
 
 
 if __name__ == "__main__":

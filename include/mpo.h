@@ -143,6 +143,18 @@ int mpo_apply_layer(mpo_handle h, int parity, const double *gates, const double 
  * sweep; for tests and custom schedules. Same gate / p formats as above. */
 int mpo_apply_gate(mpo_handle h, int bond, const double *gate, double p);
 
+/* The two-site block theta' = M (A_b A_{b+1}) of a noisy gate on ABI bond b
+ * (App. A: the superoperator applied to the contracted sites, before the
+ * truncated SVD), (4 chi_b) x (4 chi_{b+2}) row-major, row (a, I_b) =
+ * 4 a + I_b, column (I_{b+1}, c) = chi_{b+2} I_{b+1} + c; complex128 for
+ * MPO_FP64 / MPO_MIXED_FP32 handles, complex64 for MPO_FP32, in the handle's
+ * normalisation (the MPO's scalar factor, kept apart as a log-norm, is not
+ * applied: multiply by exp(log-norm) for the block of rho). The centre is
+ * moved onto the bond (the state is unchanged otherwise) and nothing is
+ * truncated. gate / p as for mpo_apply_gate; out: host or device buffer of
+ * rows x cols entries, or NULL to query *rows, *cols only. Synchronises. */
+int mpo_theta(mpo_handle h, int bond, const double *gate, double p, void *out, int *rows, int *cols);
+
 /* Apply a general 16x16 two-site superoperator (row 4*I_l + I_{l+1}, column
  * 4*J_l + J_{l+1}, App. A convention), complex128 interleaved [16][16][2],
  * host pointer, on ABI bond b. Sec. 2.2 notes the method covers any
@@ -261,6 +273,10 @@ int mpo_profile_read(mpo_handle h, int cls, const char **name, double *ms, long 
 
 /* Jacobi sweeps summed over the SVD launches recorded since mpo_profile(h, 1). */
 long long mpo_profile_sweeps(mpo_handle h);
+
+/* MPO_MIXED_FP32: subspace-iteration steps summed over the truncated SVDs
+ * recorded since mpo_profile(h, 1) (0 for the other forms). */
+long long mpo_profile_steps(mpo_handle h);
 
 /* Wall time (ms) spent by the block Jacobi SVD in its three phases (Gram
  * partials, pair eigen-solves, rotation apply; grid-barrier waits included),

@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(256) onesided_jacobi_kernel(cplx<T>* X, int r,
         cplx<T>* xp = X + (size_t)p * ldx;
         cplx<T>* xq = X + (size_t)q * ldx;
         T a = T(0), b = T(0), gr = T(0), gi = T(0);
-#pragma unroll 4
+#pragma unroll 16
         for (int j = lane; j < c; j += 32) {
           const cplx<T> x = ldcg(&xp[j]), y = ldcg(&xq[j]);
           a = fma(x.x, x.x, fma(x.y, x.y, a));
@@ -514,7 +514,7 @@ __global__ void __launch_bounds__(256) onesided_jacobi_kernel(cplx<T>* X, int r,
         if (sn == T(0)) continue;
         const T ur = (T)((double)gr / agd), ui = (T)((double)gi / agd);
         if (lane == 0) atomicAdd(&ctl->active[sweep], 1);
-#pragma unroll 4
+#pragma unroll 16
         for (int j = lane; j < c; j += 32) {
           const cplx<T> x = ldcg(&xp[j]), y = ldcg(&xq[j]);
           const cplx<T> uy = cmul<T>(mk<T>(ur, ui), y);
@@ -523,7 +523,7 @@ __global__ void __launch_bounds__(256) onesided_jacobi_kernel(cplx<T>* X, int r,
         }
         cplx<T>* tp = Ut + (size_t)p * r;
         cplx<T>* tq = Ut + (size_t)q * r;
-#pragma unroll 4
+#pragma unroll 16
         for (int j = lane; j < r; j += 32) {
           const cplx<T> x = ldcg(&tp[j]), y = ldcg(&tq[j]);
           const cplx<T> uy = cmul<T>(mk<T>(ur, -ui), y);

@@ -141,6 +141,9 @@ struct mpo_ctx {
   double* mx_d = nullptr;          // column scales of a Cholesky QR pass
   unsigned long long mx_seed = 0;  // start-basis counter
   int mx_last_steps = 0;           // subspace steps taken by the last factorisation
+  int mx_cur_bond = -1;            // bond of the gate being factorised (-1: not a gate)
+  std::vector<int> mx_bond_steps;  // subspace steps the last gate on each bond needed
+  long long prof_steps = 0;        // subspace steps since profiling was switched on
   OSCtl* mx_eosctl = nullptr;      // control block of the FP64 Rayleigh-Ritz eigen-solve
   int* mx_chst = nullptr;          // set when a Cholesky pivot was not positive
   OzWork oz;                       // FP64-accurate tensor-core GEMM scratch (precision form)
@@ -290,7 +293,7 @@ static int grid_for(size_t work, int num_sms) {
 
 template <typename T>
 static cudaError_t launch_onesided(cudaStream_t st, cplx<T>* X, int r, int c, int ldx, cplx<T>* Ut, T* w, OSCtl* ctl,
-                                   int max_sweeps, double timeout_s, int num_sms) {
+                                   int max_sweeps, double timeout_s, int num_sms, double tol_min = 0.0) {
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, onesided_jacobi_kernel<T>, 256, 0);
   if (e != cudaSuccess) return e;
@@ -304,7 +307,7 @@ static cudaError_t launch_onesided(cudaStream_t st, cplx<T>* X, int r, int c, in
   if (e != cudaSuccess) return e;
   // rows count as orthogonal once |<x_p, x_q>| <= 2 eps sqrt(c) ||x_p|| ||x_q||,
   // the rounding level of the length-c dot product itself
-  const T tol_rel = (T)(2.0 * eps_of<T>::value * std::sqrt((double)std::max(c, 1)));
+  const T tol_rel = (T)std::max(tol_min, 2.0 * eps_of<T>::value * std::sqrt((double)std::max(c, 1)));
   const T floor_rel = eps_of<T>::value * eps_of<T>::value;
   long long timeout_ns = (long long)(timeout_s * 1e9);
   void* args[] = {&X, &r, &c, &ldx, &Ut, &w, &ctl, &max_sweeps, (void*)&tol_rel, (void*)&floor_rel, &timeout_ns};
@@ -389,9 +392,16 @@ static cudaError_t oz_gemm(cudaStream_t st, int M, int N, int K, const double2* 
   const size_t Kp = 2 * (size_t)K8;
   if ((size_t)oz::S * Mp * Kp > w.a_cap || (size_t)oz::S * Nrp * Kp > w.b_cap || Mp > w.e_cap || Nrp / 2 > w.e_cap)
     return cudaErrorInvalidValue;
-  const int g = std::max(1, std::min(num_sms * 8, (std::max(M, N) + 255) / 256 * 8));
-  oz_row_exp_kernel<<<g, 256, 0, st>>>(A, lda, opA, M, K, w.ea);
-  oz_col_exp_kernel<<<g, 256, 0, st>>>(B, ldb, opB, K, N, w.eb);
+  // scaling exponents: rows of op(A) are stored rows of A (op 0) or stored
+  // columns (op 1); columns of op(B) are stored columns of B (op 0) or rows
+  cudaError_t e0 = cudaMemsetAsync(w.ea, 0, sizeof(int) * (size_t)M, st);
+  if (e0 == cudaSuccess) e0 = cudaMemsetAsync(w.eb, 0, sizeof(int) * (size_t)N, st);
+  if (e0 != cudaSuccess) return e0;
+  {
+    const int Ra = opA ? K : M, Ca = opA ? M : K, Rb = opB ? N : K, Cb = opB ? K : N;
+    oz_exp_kernel<<<dim3((Ca + 31) / 32, (Ra + 255) / 256), dim3(32, 8), 0, st>>>(A, lda, Ra, Ca, opA ? 0 : 1, w.ea);
+    oz_exp_kernel<<<dim3((Cb + 31) / 32, (Rb + 255) / 256), dim3(32, 8), 0, st>>>(B, ldb, Rb, Cb, opB ? 1 : 0, w.eb);
+  }
   oz_split_a_kernel<<<dim3(K8 / 32, Mp / 32), dim3(32, 8), 0, st>>>(A, lda, opA, M, K, K8, Mp, w.ea, w.a);
   oz_split_b_kernel<<<dim3(K8 / 32, Nrp / 64), dim3(32, 8), 0, st>>>(B, ldb, opB, K, N, K8, Nrp, w.eb, w.b);
   cudaError_t e = cudaGetLastError();
@@ -450,9 +460,14 @@ static cudaError_t mx_gemm(mpo_ctx* h, int M, int N, int K, const double2* A, in
 // Functions of Matrices, Sec. 8.3): each step squares the defect
 // |Y^H Y - I|, so a basis orthonormal to ~1e-3 reaches FP64 rounding in four
 // steps. The result is left in Y (spare is scratch; the two are swapped).
-static int mx_newton_schulz(mpo_ctx* h, double2*& Y, double2*& spare, int rows, int m, int iters) {
+static int mx_newton_schulz(mpo_ctx* h, double2*& Y, double2*& spare, int rows, int m, int iters,
+                            double* defect_dev = nullptr) {
   for (int it = 0; it < iters; ++it) {
     CK(h, mx_gemm(h, m, m, rows, Y, m, 1, Y, m, 0, h->mx_G, m));
+    if (defect_dev && it == iters - 1) {   // |Y^H Y - I| entering the last step
+      defect_kernel<<<1, 1024, 0, h->st>>>(h->mx_G, m, defect_dev);
+      CK(h, cudaGetLastError());
+    }
     {
       ProfScope ps(h, PK_REFINE, 0.0, 2.0 * m * m * sizeof(double2));
       ns_multiplier_kernel<<<grid_for((size_t)m * m, h->num_sms), 256, 0, h->st>>>(h->mx_G, m);
@@ -503,7 +518,7 @@ static int chol32_rec(mpo_ctx* h, float2* A, float2* Li, int m, int k0, int s) {
 // G = Y^H Y by the FP64-class product, A = fl32(D G D) + shift I with
 // D = diag(G)^{-1/2}, the FP32 factorisation A = L L^H with L^{-1}, and
 // Y <- Y D L^{-H} by the FP64-class product (result in Y; spare is scratch).
-// The shift, 8 m u_32, lies above the FP32 rounding of A and of its
+// The shift, 8 m u_32, bounds the FP32 rounding of A and of its
 // factorisation, so A stays positive definite whatever the conditioning of
 // Y; a pass takes a condition number kappa of Y to about sqrt(shift) kappa
 // (and no lower than 1 + shift). Mixed-precision Cholesky QR: Yamazaki,
@@ -539,14 +554,15 @@ static int mx_cholqr(mpo_ctx* h, double2*& Y, double2*& spare, int rows, int m, 
 // Subspace-iteration steps Q <- orth(X orth(X^H Q)) on Q (r x m). Each half
 // step is followed by three Cholesky QR passes, which hold the basis
 // condition number near 1 although every product multiplies it by up to
-// sigma_1 / sigma_m.
+// sigma_1 / sigma_m (each pass divides it by about 30).
 static int mx_subspace_steps(mpo_ctx* h, const double2* X, int r, int c, int ldx, int m, int steps) {
+  const int passes = 3;
   for (int it = 0; it < steps; ++it) {
     CK(h, mx_gemm(h, c, m, r, X, ldx, 1, h->mx_Q, m, 0, h->mx_T, m));     // T = X^H Q (c x m)
-    int rc = mx_cholqr(h, h->mx_T, h->mx_B, c, m, 3);
+    int rc = mx_cholqr(h, h->mx_T, h->mx_B, c, m, passes);
     if (rc) return rc;
     CK(h, mx_gemm(h, r, m, c, X, ldx, 0, h->mx_T, m, 0, h->mx_Q, m));     // Q = X T (r x m)
-    rc = mx_cholqr(h, h->mx_Q, h->mx_Q2, r, m, 3);
+    rc = mx_cholqr(h, h->mx_Q, h->mx_Q2, r, m, passes);
     if (rc) return rc;
   }
   return MPO_OK;
@@ -572,6 +588,11 @@ static int msvd_select(mpo_ctx* h, double2* X, int r, int c, int ldx, int cap, b
     CK(h, cudaGetLastError());
   }
   int rc = MPO_OK, steps = 0;
+  // the step count this bond needed last time, plus one (the spectra of
+  // successive gates on a bond change slowly, and a step costs far less than
+  // the second FP32 Rayleigh-Ritz step that too few steps force)
+  const int remembered = (h->mx_cur_bond >= 0 && h->mx_cur_bond < (int)h->mx_bond_steps.size())
+                             ? h->mx_bond_steps[h->mx_cur_bond] : 0;
   if (iterate) {
     // 1. seeded Gaussian start and the first steps of the subspace iteration
     {
@@ -583,32 +604,41 @@ static int msvd_select(mpo_ctx* h, double2* X, int r, int c, int ldx, int cap, b
     CK(h, mx_gemm(h, r, m, c, X, ldx, 0, h->mx_T, m, 0, h->mx_Q, m));     // Q = X Omega
     rc = mx_cholqr(h, h->mx_Q, h->mx_Q2, r, m, 3);
     if (rc) return rc;
-    steps = std::max(1, h->mx_steps);
+    steps = std::max(std::max(1, h->mx_steps), remembered > 0 ? remembered + 1 : 0);
     rc = mx_subspace_steps(h, X, r, c, ldx, m, steps);
     if (rc) return rc;
   }
-  // 2. FP32 Rayleigh-Ritz (stage 1), repeated after further steps until the
-  // FP32 Ritz values show the iteration converged: the leading cap
-  // directions have components outside span(Q) of order
-  // (sigma_{m+1} / sigma_cap)^(2 steps), estimated from the Ritz values as
-  // (w_m / w_cap)^steps and required below 1e-8
+  // 2. FP32 Rayleigh-Ritz (stage 1). The leading cap directions keep
+  // components outside span(Q) of order (sigma_{m+1} / sigma_cap)^(2 steps),
+  // estimated from the FP32 Ritz values as (w_m / w_cap)^steps; above 1e-7
+  // the iteration takes the steps that bring the estimate to 1e-8 and the
+  // FP32 step is repeated (the kept-theta error is about 2e-2 of the estimate)
   for (;;) {
+    // the FP32 solve runs on M = Q^H X T (m x m; T the orthonormal basis of
+    // the last half step, so M M^H = Q^H X X^H Q up to the iteration's
+    // residual) rather than on B = Q^H X (m x c), and stops at relative
+    // couplings of 3e-5: the first-order correction below and the FP64 step
+    // remove what the FP32 solve leaves
+    const int c1 = iterate ? m : c;
     if (iterate) {
-      rc = mx_newton_schulz(h, h->mx_Q, h->mx_Q2, r, m, 2);
+      rc = mx_newton_schulz(h, h->mx_Q, h->mx_Q2, r, m, 2, h->scal + 3);
+      if (rc) return rc;
+      rc = mx_newton_schulz(h, h->mx_T, h->mx_B, c, m, 2, h->scal + 4);
       if (rc) return rc;
       CK(h, mx_gemm(h, m, c, r, h->mx_Q, m, 1, X, ldx, 0, h->mx_B, c));   // B = Q^H X (m x c)
+      CK(h, mx_gemm(h, m, m, c, h->mx_B, c, 0, h->mx_T, m, 0, h->mx_W, m));  // M = B T (m x m)
     }
     {
-      ProfScope ps(h, PK_CONVERT, 0.0, (double)m * c * (sizeof(double2) + sizeof(float2)));
-      to_fp32_kernel<<<grid_for((size_t)m * c, h->num_sms), 256, 0, h->st>>>(iterate ? h->mx_B : X, m, c,
-                                                                             iterate ? c : ldx, h->mx_a32);
+      ProfScope ps(h, PK_CONVERT, 0.0, (double)m * c1 * (sizeof(double2) + sizeof(float2)));
+      to_fp32_kernel<<<grid_for((size_t)m * c1, h->num_sms), 256, 0, h->st>>>(iterate ? h->mx_W : X, m, c1,
+                                                                              iterate ? m : ldx, h->mx_a32);
       CK(h, cudaGetLastError());
     }
     {
-      const double fm = m, fc = c;
+      const double fm = m, fc = c1;
       ProfScope ps(h, disc ? PK_SVD : PK_SVD_SWEEP, 4.0 * fm * fm * fc, (2.0 * fm * fc + fm * fm) * sizeof(float2));
-      CK(h, launch_onesided<float>(h->st, h->mx_a32, m, c, c, h->mx_ut32, h->mx_w32, h->osctl,
-                                   h->opts.eig_max_sweeps, h->opts.barrier_timeout_s, h->num_sms));
+      CK(h, launch_onesided<float>(h->st, h->mx_a32, m, c1, c1, h->mx_ut32, h->mx_w32, h->osctl,
+                                   h->opts.eig_max_sweeps, h->opts.barrier_timeout_s, h->num_sms, 3e-5));
     }
     {
       ProfScope ps(h, PK_SELECT, 0.0, (double)m * (sizeof(float) + sizeof(int) + sizeof(double)));
@@ -616,17 +646,20 @@ static int msvd_select(mpo_ctx* h, double2* X, int r, int c, int ldx, int cap, b
                                  nullptr, nullptr, nullptr));
     }
     if (!iterate) break;
-    double lam[2];
-    CK(h, cudaMemcpyAsync(&lam[0], h->mx_lam32 + (cap - 1), sizeof(double), cudaMemcpyDeviceToHost, h->st));
-    CK(h, cudaMemcpyAsync(&lam[1], h->mx_lam32 + (m - 1), sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    double rd[4];   // w_cap, w_m, the two orthonormality defects
+    CK(h, cudaMemcpyAsync(&rd[0], h->mx_lam32 + (cap - 1), sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(h, cudaMemcpyAsync(&rd[1], h->mx_lam32 + (m - 1), sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(h, cudaMemcpyAsync(&rd[2], h->scal + 3, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
     CK(h, cudaMemcpyAsync(&h->hs->ctl, &h->osctl->g, sizeof(GridCtl), cudaMemcpyDeviceToHost, h->st));
     CK(h, cudaMemcpyAsync(&h->hs->chol_status, h->mx_chst, sizeof(int), cudaMemcpyDeviceToHost, h->st));
     if (h->use_oz) CK(h, cudaMemcpyAsync(&h->hs->oz_err, h->oz.status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
     CK(h, cudaStreamSynchronize(h->st));
     rc = msvd_status(h);
     if (rc) return rc;
-    const double rho2 = lam[0] > 0.0 ? std::max(0.0, lam[1]) / lam[0] : 0.0;
-    if (steps >= kMixedMaxSteps || rho2 <= 0.0 || std::pow(rho2, steps) <= 1e-8) break;
+    if (!(std::max(rd[2], rd[3]) <= 1e-3))
+      return fail(h, MPO_ERR_NOCONV, "subspace basis not orthonormal after Cholesky QR");
+    const double rho2 = rd[0] > 0.0 ? std::max(0.0, rd[1]) / rd[0] : 0.0;
+    if (steps >= kMixedMaxSteps || rho2 <= 0.0 || std::pow(rho2, steps) <= 1e-7) break;
     const int need = rho2 < 1.0 ? (int)std::ceil(std::log(1e-8) / std::log(rho2)) : kMixedMaxSteps;
     const int more = std::max(1, std::min(need, kMixedMaxSteps) - steps);
     rc = mx_subspace_steps(h, X, r, c, ldx, m, more);
@@ -634,6 +667,9 @@ static int msvd_select(mpo_ctx* h, double2* X, int r, int c, int ldx, int cap, b
     steps += more;
   }
   h->mx_last_steps = steps;
+  if (h->prof) h->prof_steps += steps;
+  if (iterate && h->mx_cur_bond >= 0 && h->mx_cur_bond < (int)h->mx_bond_steps.size())
+    h->mx_bond_steps[h->mx_cur_bond] = steps;
   // 3. the mp leading FP32 Ritz directions V_P (V = U32 in descending order,
   // promoted), corrected to first order for their error along the other
   // m - mp directions (the FP32 solve leaves couplings of 2 eps_32 sqrt(c)
@@ -965,9 +1001,11 @@ static int gate_update(mpo_ctx* h, int i, const cplx<T>* M) {
     CK(h, cudaGetLastError());
   }
   int k = 0;
+  h->mx_cur_bond = i;
   if (mL <= mR) {
     // theta' = U X', rows of X' = Lambda W^H
     rc = svd_select<T>(h, th, mL, mR, mR, h->chi_max, true, nullptr, nullptr, &k);
+    h->mx_cur_bond = -1;
     if (rc) return rc;
     CK(h, gather_rows<T>(h, (cplx<T>*)h->vecs, mL, mL, k, 1, (int)h->vecs_conj, 0, A0, k));   // U_k -> site i
     CK(h, gather_rows<T>(h, th, mR, mR, k, 0, 0, 3, A1, mR));                    // Lambda W^H / ||kept||
@@ -976,6 +1014,7 @@ static int gate_update(mpo_ctx* h, int i, const cplx<T>* M) {
     cplx<T>* Y = (cplx<T>*)h->theta2;
     CK(h, conj_transpose<T>(h, th, mL, mR, mR, Y, mL));
     rc = svd_select<T>(h, Y, mR, mL, mL, h->chi_max, true, nullptr, nullptr, &k);
+    h->mx_cur_bond = -1;
     if (rc) return rc;
     CK(h, gather_rows<T>(h, (cplx<T>*)h->vecs, mR, mR, k, 0, 1 ^ (int)h->vecs_conj, 2, A1, mR));   // Lambda U^H / ||kept||
     CK(h, gather_rows<T>(h, Y, mL, mL, k, 1, 1, 1, A0, k));                      // X'^H Lambda^-1
@@ -1033,6 +1072,29 @@ static int stage_gates(mpo_ctx* h, int ng, const double* gates, const double* p,
   }
   build_superop_kernel<T><<<ng, 256, 0, h->st>>>(dg, dp, stride, (cplx<T>*)h->Ms);
   CK(h, cudaGetLastError());
+  return MPO_OK;
+}
+
+// theta' = M (A_i A_{i+1}) of a noisy gate on ABI bond i, formed by the
+// kernels of gate_update (centre move, contraction, superoperator) and copied
+// to out without truncation; the state keeps its centre on the bond.
+template <typename T>
+static int theta_t(mpo_ctx* h, int i, const double* gate, double p, void* out, int* rows, int* cols) {
+  int rc = move_centre<T>(h, i, i + 1);
+  if (rc) return rc;
+  const int chiL = h->chi[i], chiM = h->chi[i + 1], chiR = h->chi[i + 2];
+  *rows = 4 * chiL;
+  *cols = 4 * chiR;
+  if (!out) return MPO_OK;
+  rc = stage_gates<T>(h, 1, gate, &p, 0);
+  if (rc) return rc;
+  cplx<T>* th = (cplx<T>*)h->theta;
+  CK(h, gemm_p<T>(h, 4 * chiL, 4 * chiR, chiM, S_<T>(h, i), chiM, 0, S_<T>(h, i + 1), 4 * chiR, 0, th, 4 * chiR));
+  apply_superop_kernel<T><<<grid_for((size_t)chiL * chiR, h->num_sms), 256, 0, h->st>>>(th, chiL, chiR,
+                                                                                         (const cplx<T>*)h->Ms);
+  CK(h, cudaGetLastError());
+  CK(h, cudaMemcpyAsync(out, th, (size_t)16 * chiL * chiR * sizeof(cplx<T>), cudaMemcpyDefault, h->st));
+  CK(h, cudaStreamSynchronize(h->st));
   return MPO_OK;
 }
 
@@ -1281,6 +1343,7 @@ int mpo_init(mpo_handle* out, int n, int chi_max, mpo_precision prec, void* stre
   // precision form: subspace iteration on chi_max + oversample directions,
   // FP32 and FP64 Rayleigh-Ritz steps
   h->mx_over = h->opts.oversample > 0 ? h->opts.oversample : (h->opts.oversample < 0 ? 0 : chi_max);
+  h->mx_bond_steps.assign(n, 0);
   h->mx_steps = h->opts.refine_steps > 0 ? std::min(h->opts.refine_steps, kMixedMaxSteps) : (h->opts.refine_steps < 0 ? 1 : kMixedSteps);
   h->mx_mcap = std::min(m, chi_max + h->mx_over);
   // FP64-accurate products on the tensor cores (BF16 slices) unless switched off
@@ -1326,7 +1389,7 @@ int mpo_init(mpo_handle* out, int n, int chi_max, mpo_precision prec, void* stre
   ok = ok && alloc((void**)&h->dsup, 256 * sizeof(double2));
   ok = ok && alloc_factor_ws(h, m, mx_ccap, bj_nch);
   if (ok && h->use_oz) ok = alloc_oz(h->oz, std::max(m, mx_ccap), &h->bytes);
-  ok = ok && alloc((void**)&h->scal, 4 * sizeof(double));
+  ok = ok && alloc((void**)&h->scal, 8 * sizeof(double));
   ok = ok && alloc((void**)&h->dS, (size_t)(n - 1) * sizeof(double));
   ok = ok && alloc((void**)&h->dschmidt, (size_t)(n - 1) * chi_max * sizeof(double));
   ok = ok && alloc((void**)&h->tv0, (size_t)(chi_max + 1) * sizeof(double2));
@@ -1347,7 +1410,7 @@ int mpo_init(mpo_handle* out, int n, int chi_max, mpo_precision prec, void* stre
       return init_fail(h, MPO_ERR_CUDA, "initial state upload failed");
   }
   if (cudaMemsetAsync(h->tc_status, 0, sizeof(int), h->st) != cudaSuccess ||
-      cudaMemsetAsync(h->scal, 0, 4 * sizeof(double), h->st) != cudaSuccess ||
+      cudaMemsetAsync(h->scal, 0, 8 * sizeof(double), h->st) != cudaSuccess ||
       cudaMemsetAsync(h->dS, 0, (size_t)(n - 1) * sizeof(double), h->st) != cudaSuccess ||
       cudaStreamSynchronize(h->st) != cudaSuccess)
     return init_fail(h, MPO_ERR_CUDA, "initial state upload failed");
@@ -1417,6 +1480,14 @@ int mpo_apply_gate(mpo_handle h, int bond, const double* gate, double p) {
   }
   int rc = stage_gates<float>(h, 1, gate, &p, 0);
   return rc ? rc : gate_update<float>(h, bond, (const float2*)h->Ms);
+}
+
+int mpo_theta(mpo_handle h, int bond, const double* gate, double p, void* out, int* rows, int* cols) {
+  GUARD(h);
+  if (bond < 0 || bond > h->n - 2 || !gate || !rows || !cols) return fail(h, MPO_ERR_ARG, "bad bond, gate or dims");
+  if (!(p >= 0.0 && p <= 1.0)) return fail(h, MPO_ERR_ARG, "p must lie in [0, 1]");
+  return dsite(h) ? theta_t<double>(h, bond, gate, p, out, rows, cols)
+                  : theta_t<float>(h, bond, gate, p, out, rows, cols);
 }
 
 int mpo_apply_superop(mpo_handle h, int bond, const double* M) {
@@ -1510,6 +1581,7 @@ int mpo_profile(mpo_handle h, int enable) {
   if (enable) {
     for (int i = 0; i < PK_NCLASS; ++i) { h->prof_ms[i] = 0; h->prof_n[i] = 0; h->prof_flops[i] = 0; h->prof_bytes[i] = 0; }
     h->prof_sweeps = 0;
+    h->prof_steps = 0;
     for (int i = 0; i < 3; ++i) h->prof_phase_ns[i] = 0;
   }
   h->prof = enable != 0;
@@ -1530,6 +1602,8 @@ int mpo_profile_read(mpo_handle h, int cls, const char** name, double* ms, long 
 }
 
 long long mpo_profile_sweeps(mpo_handle h) { return h ? h->prof_sweeps : 0; }
+
+long long mpo_profile_steps(mpo_handle h) { return h ? h->prof_steps : 0; }
 
 int mpo_profile_phases(mpo_handle h, double* ms3) {
   GUARD(h);
@@ -1679,14 +1753,14 @@ int mpo_svd_truncated(int r, int c, const void* A, int cap, mpo_precision prec, 
   h->use_oz = h->mixed && h->opts.tensor_cores >= 0;
   const size_t nch = (size_t)(c + JCW - 1) / JCW + 1;
   bool ok = ws_alloc(h, &h->theta, (size_t)r * c * h->esz) && alloc_factor_ws(h, r, c, nch) &&
-            ws_alloc(h, (void**)&h->scal, 4 * sizeof(double));
+            ws_alloc(h, (void**)&h->scal, 8 * sizeof(double));
   if (ok && h->use_oz) ok = alloc_oz(h->oz, c, &h->bytes);
   if (ok && cudaMallocHost((void**)&h->hs, sizeof(HostSync)) != cudaSuccess) { cudaGetLastError(); h->hs = nullptr; ok = false; }
   if (!ok) { mpo_free(h); g_last_init_error = "mpo_svd_truncated: allocation failed"; return MPO_ERR_OOM; }
   int rc = MPO_OK, kk = 0;
   auto ck = [&](cudaError_t e) { if (rc == MPO_OK && e != cudaSuccess) { rc = MPO_ERR_CUDA; g_last_init_error = cudaGetErrorString(e); } };
   ck(cudaMemcpyAsync(h->theta, A, (size_t)r * c * h->esz, cudaMemcpyDeviceToDevice, h->st));
-  ck(cudaMemsetAsync(h->scal, 0, 4 * sizeof(double), h->st));
+  ck(cudaMemsetAsync(h->scal, 0, 8 * sizeof(double), h->st));
   ck(cudaMemsetAsync(h->tc_status, 0, sizeof(int), h->st));
   if (rc == MPO_OK) {
     rc = prec != MPO_FP32 ? svd_select<double>(h, (double2*)h->theta, r, c, c, cap, true, nullptr, nullptr, &kk)

@@ -7,7 +7,7 @@
 // Splitting. Every row i of op(A) (every column j of op(B)) gets a power of
 // two 2^e_i bounding its entries; each real entry x = v / 2^e_i in (-1, 1)
 // is written as sum_{t=1..S} a_t 2^{-7t} with integers |a_1| <= 128,
-// |a_t| <= 64 for t >= 2 (a_t = rint of the remaining fraction times 128),
+// |a_t| <= 64 for t >= 2 (the balanced base-128 digits of round(x 2^{7S})),
 // so every slice value a_t 2^{-7t} is exact in BF16 and every product
 // a_t b_u 2^{-7(t+u)} is exact in FP32. Keeping the products with
 // t + u <= S + 1 leaves a relative error of about 2^{-7S} of |row| |column|.
@@ -78,46 +78,73 @@ __device__ __forceinline__ uint64_t desc(uint32_t addr, uint32_t lbo) {
 }
 }  // namespace oz
 
-// e[i] = the exponent of the largest |Re| or |Im| in row i of op(A)
-// (M x K; op 0: A[i * lda + k], op 1: conj(A[k * lda + i])), in the frexp
-// convention (max < 2^e); 0 for a zero row. Grid-stride over rows.
-__global__ void oz_row_exp_kernel(const double2* __restrict__ A, int lda, int op, int M, int K, int* __restrict__ e) {
-  if (op == 0) {   // one warp per row, lanes along the row
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int i = warp; i < M; i += nw) {
-      double mx = 0.0;
-      for (int k = lane; k < K; k += 32) {
-        const double2 v = A[(size_t)i * lda + k];
-        mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
-      }
-      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      if (lane == 0) { int ex = 0; if (mx > 0.0) frexp(mx, &ex); e[i] = ex; }
+// Scaling exponents. raw[i] = the largest biased FP64 exponent field among
+// the real and imaginary parts of row i of op(A) (or column j of op(B)),
+// gathered with integer atomicMax (raw zeroed beforehand); the scaling
+// exponent is then oz_ex(raw) = raw - 1022 (the frexp exponent of the row's
+// largest entry, so every |x| < 2^oz_ex), or 0 for a zero row.
+__device__ __forceinline__ int oz_ex(int raw) { return raw > 0 ? raw - 1022 : 0; }
+__device__ __forceinline__ int oz_bexp(double v) { return (int)((__double_as_longlong(v) >> 52) & 0x7FF); }
+
+// The stored matrix (R rows x C columns, leading dimension ld) is scanned in
+// 32-column x 256-row tiles, block (32, 8); by_row = 1 reduces along each
+// stored row (raw indexed by stored row), 0 along each stored column (raw
+// indexed by stored column). One atomic per warp-row or per tile column.
+__global__ void oz_exp_kernel(const double2* __restrict__ X, int ld, int R, int C, int by_row, int* __restrict__ raw) {
+  __shared__ int red[8][33];
+  const int c = blockIdx.x * 32 + threadIdx.x, r0 = blockIdx.y * 256, ty = threadIdx.y;
+  int mcol = 0;
+  for (int r = r0 + ty; r < min(R, r0 + 256); r += 8) {
+    int v = 0;
+    if (c < C) {
+      const double2 x = X[(size_t)r * ld + c];
+      v = max(oz_bexp(x.x), oz_bexp(x.y));
     }
-  } else {         // one thread per row, reading a column of A (coalesced across threads)
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
-      double mx = 0.0;
-      for (int k = 0; k < K; ++k) {
-        const double2 v = A[(size_t)k * lda + i];
-        mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
-      }
-      int ex = 0;
-      if (mx > 0.0) frexp(mx, &ex);
-      e[i] = ex;
+    if (by_row) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+      if (threadIdx.x == 0 && v > 0) atomicMax(&raw[r], v);
+    } else {
+      mcol = max(mcol, v);
+    }
+  }
+  if (!by_row) {
+    red[ty][threadIdx.x] = mcol;
+    __syncthreads();
+    if (ty == 0) {
+      int v = red[0][threadIdx.x];
+#pragma unroll
+      for (int i = 1; i < 8; ++i) v = max(v, red[i][threadIdx.x]);
+      if (c < C && v > 0) atomicMax(&raw[c], v);
     }
   }
 }
 
-// The S pre-scaled slices of v / 2^ex (|v| < 2^ex): out[t] = a_{t+1} 2^{-7(t+1)}.
+// The S slices of x / 2^ex (|x| < 2^ex) by integer arithmetic on the FP64
+// bits: N = round(x 2^(7S - ex)), |N| <= 2^(7S), written in balanced base-128
+// digits N = sum_t a_t 2^(7(S - t)) (a_t in [-64, 63] for t >= 2 and
+// |a_1| <= 128); out[t] = a_{t+1} 2^{-7(t+1)}, exact in BF16. The error
+// |x / 2^ex - sum| <= 2^(-7S - 1). No FP64 arithmetic (that unit runs at
+// 1/64 of the FP32 rate on this part).
 __device__ __forceinline__ void oz_slices(double v, int ex, float* out) {
-  double x = ldexp(v, -ex);
-#pragma unroll
-  for (int t = 0; t < oz::S; ++t) {
-    const double y = x * 128.0;
-    const double a = rint(y);
-    out[t] = (float)ldexp(a, -7 * (t + 1));
-    x = y - a;
+  const long long bits = __double_as_longlong(v);
+  const int be = (int)((bits >> 52) & 0x7FF);
+  long long n = 0;
+  if (be > 0) {
+    const long long mant = (bits & 0xFFFFFFFFFFFFFll) | (1ll << 52);
+    const int sh = 1075 - 7 * oz::S + ex - be;     // right shift taking mant 2^(be-1075) to units of 2^(ex - 7S)
+    if (sh < 63) {
+      const long long mag = sh > 0 ? (mant + (1ll << (sh - 1))) >> sh : mant << (-sh);
+      n = bits < 0 ? -mag : mag;
+    }
   }
+#pragma unroll
+  for (int t = oz::S - 1; t >= 1; --t) {
+    const long long d = ((n + 64) & 127) - 64;
+    out[t] = __int2float_rn((int)d) * __int_as_float((127 - 7 * (t + 1)) << 23);
+    n = (n - d) >> 7;
+  }
+  out[0] = __int2float_rn((int)n) * __int_as_float((127 - 7) << 23);
 }
 
 // Slices of op(A)' = [Re | Im] into Asl[t][i][c] (S x Mp x Kp, row-major,
@@ -145,7 +172,7 @@ __global__ void oz_split_a_kernel(const double2* __restrict__ A, int lda, int op
   for (int r = ty; r < 32; r += 8) {
     const int i = i0 + r, k = k0 + tx;
     const double2 v = tile[r][tx];
-    const int ex = i < M ? e[i] : 0;
+    const int ex = i < M ? oz_ex(e[i]) : 0;
     float sr[oz::S], si[oz::S];
     oz_slices(v.x, ex, sr);
     oz_slices(v.y, ex, si);
@@ -153,35 +180,6 @@ __global__ void oz_split_a_kernel(const double2* __restrict__ A, int lda, int op
     for (int t = 0; t < oz::S; ++t) {
       Asl[t * sstride + (size_t)i * Kp + k] = __float2bfloat16_rn(sr[t]);
       Asl[t * sstride + (size_t)i * Kp + K8 + k] = __float2bfloat16_rn(si[t]);
-    }
-  }
-}
-
-// f[j] = exponent of the largest |Re| or |Im| in column j of op(B) (K x N;
-// op 0: B[k * ldb + j], op 1: conj(B[j * ldb + k])); 0 for a zero column.
-__global__ void oz_col_exp_kernel(const double2* __restrict__ B, int ldb, int op, int K, int N, int* __restrict__ f) {
-  if (op == 1) {   // column j of op(B) is row j of B: one warp per column
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int j = warp; j < N; j += nw) {
-      double mx = 0.0;
-      for (int k = lane; k < K; k += 32) {
-        const double2 v = B[(size_t)j * ldb + k];
-        mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
-      }
-      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      if (lane == 0) { int ex = 0; if (mx > 0.0) frexp(mx, &ex); f[j] = ex; }
-    }
-  } else {
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
-      double mx = 0.0;
-      for (int k = 0; k < K; ++k) {
-        const double2 v = B[(size_t)k * ldb + j];
-        mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
-      }
-      int ex = 0;
-      if (mx > 0.0) frexp(mx, &ex);
-      f[j] = ex;
     }
   }
 }
@@ -211,7 +209,7 @@ __global__ void oz_split_b_kernel(const double2* __restrict__ B, int ldb, int op
   for (int r = ty; r < 32; r += 8) {
     const int j = j0 + r, k = k0 + tx;
     const double2 v = tile[r][tx];
-    const int ex = j < N ? f[j] : 0;
+    const int ex = j < N ? oz_ex(f[j]) : 0;
     float sr[oz::S], si[oz::S];
     oz_slices(v.x, ex, sr);
     oz_slices(v.y, ex, si);
@@ -364,12 +362,12 @@ __global__ void __launch_bounds__(512, 1) oz_mma_kernel(int M, int N, int Kp, co
   }
   if (!s_fail) {
     const int row = row0 + 32 * lg + lane;
-    const int er = row < M ? eA[row] : 0;
+    const int er = row < M ? oz_ex(eA[row]) : 0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int j = (rcol0 >> 1) + 8 * cg + q;     // complex column: real part 2q, imaginary 2q + 1
       if (row >= M || j >= N) continue;
-      const int sc = er + eB[j];
+      const int sc = er + oz_ex(eB[j]);
       double re = (double)hi[2 * q] + (double)lo[2 * q];
       double im = (double)hi[2 * q + 1] + (double)lo[2 * q + 1];
       re = ldexp(re, sc) * alpha;

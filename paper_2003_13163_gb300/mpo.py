@@ -21,9 +21,10 @@ ERRORS = {0: "MPO_OK", -1: "MPO_ERR_ARG", -2: "MPO_ERR_CUDA", -3: "MPO_ERR_OOM",
 EXPORTS = ["mpo_default_opts", "mpo_init", "mpo_apply_layer", "mpo_apply_gate", "mpo_apply_superop", "mpo_sweep",
            "mpo_entropy", "mpo_schmidt", "mpo_bond_dims", "mpo_get_site", "mpo_to_dense", "mpo_centre",
            "mpo_device_bytes", "mpo_free", "mpo_last_error", "mpo_eigh", "mpo_svd", "mpo_version",
-           "mpo_profile", "mpo_profile_read", "mpo_profile_sweeps", "mpo_profile_phases", "mpo_svd_static",
+           "mpo_profile", "mpo_profile_read", "mpo_profile_sweeps", "mpo_profile_steps", "mpo_profile_phases", "mpo_svd_static",
            "mpo_probability", "mpo_sample", "mpo_gemm", "mpo_svd_last_stats",
-           "mpo_init_batch", "mpo_apply_layer_batch", "mpo_batch_instance", "mpo_svd_truncated", "mpo_gemm_ex"]
+           "mpo_init_batch", "mpo_apply_layer_batch", "mpo_batch_instance", "mpo_svd_truncated", "mpo_gemm_ex",
+           "mpo_theta"]
 
 
 class MPOError(RuntimeError):
@@ -75,6 +76,7 @@ def load_library(path: str | None = None):
         "mpo_profile": (I, [P, I]),
         "mpo_profile_read": (I, [P, I, ctypes.POINTER(ctypes.c_char_p), DP, ctypes.POINTER(ctypes.c_longlong), DP, DP]),
         "mpo_profile_sweeps": (ctypes.c_longlong, [P]),
+        "mpo_profile_steps": (ctypes.c_longlong, [P]),
         "mpo_profile_phases": (I, [P, DP]),
         "mpo_svd_static": (I, [I, I, P, P, P, I, I, P]),
         "mpo_probability": (I, [P, I, P, P]),
@@ -86,6 +88,7 @@ def load_library(path: str | None = None):
         "mpo_batch_instance": (I, [P, I, ctypes.POINTER(P)]),
         "mpo_svd_truncated": (I, [I, I, P, I, I, ctypes.POINTER(Opts), P, P, DP, IP, P]),
         "mpo_gemm_ex": (I, [I, I, I, P, I, I, P, I, I, P, I, I, I, P]),
+        "mpo_theta": (I, [P, I, P, D, P, IP, IP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -177,9 +180,27 @@ class MPO:
             pa, stride = p, 1
         self._check(self._lib.mpo_apply_layer(self.h, parity, _ptr(gates), _ptr(pa), stride))
 
-    def apply_gate(self, bond: int, U: np.ndarray, p: float) -> None:
-        U = np.ascontiguousarray(U, dtype=np.complex128)
+    def apply_gate(self, bond: int, U, p: float) -> None:
+        """One noisy gate on ABI bond `bond` (no sweep). U: (4, 4) complex128
+        numpy array, or a CUDA / pinned tensor of 32 float64 (re, im pairs)."""
+        if isinstance(U, np.ndarray):
+            U = np.ascontiguousarray(U, dtype=np.complex128)
         self._check(self._lib.mpo_apply_gate(self.h, bond, _ptr(U), float(p)))
+
+    def theta(self, bond: int, U, p: float):
+        """theta' = M (A_b A_{b+1}) of a noisy gate on ABI bond b, untruncated,
+        as a CUDA tensor (4 chi_b, 4 chi_{b+2}) (mpo_theta); the centre moves
+        onto the bond."""
+        import torch
+        if isinstance(U, np.ndarray):
+            U = np.ascontiguousarray(U, dtype=np.complex128)
+        r, c = ctypes.c_int(), ctypes.c_int()
+        self._check(self._lib.mpo_theta(self.h, bond, _ptr(U), float(p), None, ctypes.byref(r), ctypes.byref(c)))
+        dt = torch.complex64 if self.prec == MPO_FP32 else torch.complex128
+        out = torch.empty((r.value, c.value), dtype=dt, device="cuda")
+        self._check(self._lib.mpo_theta(self.h, bond, _ptr(U), float(p), ctypes.c_void_p(out.data_ptr()),
+                                        ctypes.byref(r), ctypes.byref(c)))
+        return out
 
     def apply_superop(self, bond: int, M: np.ndarray) -> None:
         M = np.ascontiguousarray(M, dtype=np.complex128)
@@ -258,6 +279,7 @@ class MPO:
                 break
             out[nm.value.decode()] = {"ms": ms.value, "launches": n.value, "flops": fl.value, "bytes": by.value}
         out["_sweeps"] = int(self._lib.mpo_profile_sweeps(self.h))
+        out["_steps"] = int(self._lib.mpo_profile_steps(self.h))
         ph = (ctypes.c_double * 3)()
         self._check(self._lib.mpo_profile_phases(self.h, ph))
         out["_block_jacobi_phase_ms"] = {"gram": ph[0], "pair_eig": ph[1], "apply": ph[2]}

@@ -203,3 +203,31 @@ def test_mixed_centre_mode_and_schmidt_values(M):
     assert np.abs(l64[:n] - lmx[:n]).max() < 1e-7
     m64.close()
     mmx.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_theta_export_matches_oracle(M, precision):
+    """mpo_theta (App. A: the superoperator applied to the contracted sites,
+    before truncation) against Oracle M's theta' for the first gate of step
+    11 of the same seeded circuit. The bond bases are fixed only up to
+    unitaries and the scalar factor is kept apart, so the gauge-invariant
+    normalised singular values are compared."""
+    c = random_circuit(16, 11, 0.005, 2)
+    m = M.MPO(16, 64, precision)
+    for t in range(1, 11):
+        m.apply_layer(c.parity(t), c.gates[t - 1], c.p[t - 1])
+    l0 = layer_bonds(16, c.parity(11))[0]
+    th = m.theta(l0 - 1, c.gates[10][0], float(c.p[10][0])).cpu().numpy()
+    m.close()
+    ref = oracle_thetas(16, 64, 0.005, 2, 10)[0]
+    if precision == "fp64":
+        assert th.shape == ref.shape
+    s, sr = np.linalg.svd(th, compute_uv=False), np.linalg.svd(ref, compute_uv=False)
+    # the handle keeps the MPO's scalar factor apart (its log-norm): compare
+    # the spectra normalised to unit Frobenius norm
+    s, sr = s / np.linalg.norm(s), sr / np.linalg.norm(sr)
+    # the precision form drops Schmidt values below 1e-7 of the largest at
+    # every factorisation, so its bonds may be narrower by those directions
+    k = min(len(s), len(sr))
+    np.testing.assert_allclose(s[:k], sr[:k], rtol=0, atol=(1e-10 if precision == "fp64" else 1e-7) * sr[0])
+    assert np.all(sr[k:] <= 1e-6 * sr[0])
