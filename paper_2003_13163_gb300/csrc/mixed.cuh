@@ -1,17 +1,22 @@
 // mixed.cuh - kernels of the precision form ("mixed"): the truncated SVD of
-// a complex128 matrix A whose approximate left singular basis comes from the
-// FP32 one-sided Jacobi SVD of fl32(A) and is refined in FP64:
+// a complex128 matrix A (App. A) with FP64-class products on the tensor cores
+// and FP32 solves, refined to FP64 accuracy:
 //
-//   Q <- the m leading columns of the FP32 left factor, promoted to FP64 and
-//        made orthonormal by Newton-Schulz steps Q <- Q (3 I - Q^H Q) / 2;
-//   optionally, subspace iteration Q <- orth(A A^H Q), orth = shifted
-//        CholeskyQR3, with the basis turned back towards the FP32 one;
-//   Rayleigh-Ritz: B = Q^H A, its Gram H = B B^H and the FP64 Hermitian
-//        eigen-solve H = V Lambda^2 V^H; left factor Q V, rows V^H B.
+//   subspace iteration from a seeded Gaussian start, Q <- orth(A orth(A^H Q)),
+//        orth = mixed-precision Cholesky QR (FP64-class Gram, FP32 Cholesky of
+//        the diagonally scaled Gram, FP64-class product), Newton-Schulz steps
+//        Q <- Q (3 I - Q^H Q) / 2 for the final orthonormality;
+//   FP32 Rayleigh-Ritz (one-sided Jacobi) on the iterated subspace, and a
+//        first-order correction of its leading directions for the coupling
+//        the FP32 solve leaves to the rest of the subspace;
+//   FP64 Rayleigh-Ritz on those directions: B = Q'^H A, H = B B^H and the FP64
+//        Hermitian Jacobi eigen-solve H = V Lambda^2 V^H; left factor Q' V,
+//        rows V^H B.
 //
 // The products are the engine's complex GEMM; these kernels convert, gather,
-// form the Newton-Schulz multiplier, factor the diagonal blocks of the
-// blocked Cholesky factorisation, shift a Gram matrix and make one Hermitian.
+// draw the start basis, form the Newton-Schulz multiplier and the Cholesky QR
+// factors, reduce norms and defects, make a Gram matrix Hermitian and form
+// the first-order correction.
 #pragma once
 #include "common.cuh"
 
@@ -59,13 +64,11 @@ __global__ void ns_multiplier_kernel(double2* __restrict__ G, int m) {
 // forward substitution; L goes to the lower triangle of the block in G
 // (leading dimension ldg), L^{-1} to Linv (leading dimension ldl, zeros above
 // the diagonal). A non-positive pivot sets *status (the factorisation then
-// continues with a tiny pivot so that no NaN is produced). Instantiated in
-// FP64 (NB = 32) for the FP64 Cholesky QR and in FP32 (NB = 64) for the
-// mixed-precision one.
+// continues with a tiny pivot so that no NaN is produced). The precision
+// form instantiates it in FP32 with NB = 64.
 // ---------------------------------------------------------------------------
 template <typename T, int NB>
 constexpr int chol_smem_bytes() { return 2 * NB * (NB + 1) * (int)sizeof(cplx<T>); }
-constexpr int CHOL_NB = 32;       // FP64 base block
 constexpr int CHOL32_NB = 64;     // FP32 base block
 
 template <typename T, int NB>
@@ -190,14 +193,15 @@ __global__ void add_trace_shift_kernel(double2* __restrict__ G, int m, double re
   for (int i = threadIdx.x; i < m; i += blockDim.x) G[(size_t)i * m + i].x += sh;
 }
 
-// *out = sum |A_ij|^2 over an r x c complex128 matrix (leading dimension lda),
-// accumulated in FP64. One CTA (the matrices are at most a few tens of MB).
-__global__ void __launch_bounds__(1024) frob2_kernel(const double2* __restrict__ A, int r, int c, int lda,
-                                                     double* __restrict__ out) {
-  __shared__ double red[32];
+// *out += sum |A_ij|^2 over an r x c complex128 matrix (leading dimension
+// lda), accumulated in FP64: grid-stride partial sums, one atomicAdd per CTA
+// (*out zeroed beforehand).
+__global__ void __launch_bounds__(256) frob2_kernel(const double2* __restrict__ A, int r, int c, int lda,
+                                                    double* __restrict__ out) {
+  __shared__ double red[8];
   double s = 0.0;
   const size_t total = (size_t)r * c;
-  for (size_t e = threadIdx.x; e < total; e += blockDim.x) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const double2 v = A[(e / c) * lda + e % c];
     s += v.x * v.x + v.y * v.y;
   }
@@ -206,8 +210,8 @@ __global__ void __launch_bounds__(1024) frob2_kernel(const double2* __restrict__
   __syncthreads();
   if (threadIdx.x == 0) {
     double v = 0.0;
-    for (int i = 0; i < (blockDim.x + 31) / 32; ++i) v += red[i];
-    *out = v;
+    for (int i = 0; i < 8; ++i) v += red[i];
+    atomicAdd(out, v);
   }
 }
 
@@ -258,12 +262,14 @@ __global__ void partition_correction_kernel(const double2* __restrict__ S, const
   }
 }
 
-// *out = max_ij |G_ij - delta_ij| over an m x m complex128 matrix (one CTA):
-// the orthonormality defect of a basis whose Gram matrix is G.
-__global__ void __launch_bounds__(1024) defect_kernel(const double2* __restrict__ G, int m, double* __restrict__ out) {
-  __shared__ double red[32];
+// *out = max_ij |G_ij - delta_ij| over an m x m complex128 matrix: the
+// orthonormality defect of a basis whose Gram matrix is G. Grid-stride
+// maxima, one atomicMax per CTA on the bit pattern (order-preserving for
+// non-negative doubles); *out zeroed beforehand.
+__global__ void __launch_bounds__(256) defect_kernel(const double2* __restrict__ G, int m, double* __restrict__ out) {
+  __shared__ double red[8];
   double s = 0.0;
-  for (size_t e = threadIdx.x; e < (size_t)m * m; e += blockDim.x) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < (size_t)m * m; e += (size_t)gridDim.x * blockDim.x) {
     const size_t i = e / m, j = e % m;
     const double2 g = G[e];
     s = fmax(s, hypot(g.x - (i == j ? 1.0 : 0.0), g.y));
@@ -273,7 +279,7 @@ __global__ void __launch_bounds__(1024) defect_kernel(const double2* __restrict_
   __syncthreads();
   if (threadIdx.x == 0) {
     double v = 0.0;
-    for (int i = 0; i < (blockDim.x + 31) / 32; ++i) v = fmax(v, red[i]);
-    *out = v;
+    for (int i = 0; i < 8; ++i) v = fmax(v, red[i]);
+    atomicMax((unsigned long long*)out, (unsigned long long)__double_as_longlong(v));
   }
 }

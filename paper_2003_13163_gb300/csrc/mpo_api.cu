@@ -465,7 +465,8 @@ static int mx_newton_schulz(mpo_ctx* h, double2*& Y, double2*& spare, int rows, 
   for (int it = 0; it < iters; ++it) {
     CK(h, mx_gemm(h, m, m, rows, Y, m, 1, Y, m, 0, h->mx_G, m));
     if (defect_dev && it == iters - 1) {   // |Y^H Y - I| entering the last step
-      defect_kernel<<<1, 1024, 0, h->st>>>(h->mx_G, m, defect_dev);
+      CK(h, cudaMemsetAsync(defect_dev, 0, sizeof(double), h->st));
+      defect_kernel<<<grid_for((size_t)m * m, h->num_sms), 256, 0, h->st>>>(h->mx_G, m, defect_dev);
       CK(h, cudaGetLastError());
     }
     {
@@ -584,7 +585,8 @@ static int msvd_select(mpo_ctx* h, double2* X, int r, int c, int ldx, int cap, b
   CK(h, cudaMemsetAsync(h->mx_chst, 0, sizeof(int), h->st));
   {
     ProfScope ps(h, PK_CONVERT, 0.0, (double)r * c * sizeof(double2));
-    frob2_kernel<<<1, 1024, 0, h->st>>>(X, r, c, ldx, h->scal + 2);          // total weight ||X||_F^2
+    CK(h, cudaMemsetAsync(h->scal + 2, 0, sizeof(double), h->st));
+    frob2_kernel<<<grid_for((size_t)r * c, h->num_sms), 256, 0, h->st>>>(X, r, c, ldx, h->scal + 2);   // ||X||_F^2
     CK(h, cudaGetLastError());
   }
   int rc = MPO_OK, steps = 0;
@@ -870,7 +872,8 @@ static int mx_isometry(mpo_ctx* h, double2*& Y, int rows, int r, bool* ok) {
   rc = mx_newton_schulz(h, Y, sp, rows, r, 2);
   if (rc) return rc;
   CK(h, mx_gemm(h, r, r, rows, Y, r, 1, Y, r, 0, h->mx_G, r));
-  defect_kernel<<<1, 1024, 0, h->st>>>(h->mx_G, r, h->scal + 3);
+  CK(h, cudaMemsetAsync(h->scal + 3, 0, sizeof(double), h->st));
+  defect_kernel<<<grid_for((size_t)r * r, h->num_sms), 256, 0, h->st>>>(h->mx_G, r, h->scal + 3);
   CK(h, cudaGetLastError());
   rc = mx_newton_schulz(h, Y, sp, rows, r, 1);
   if (rc) return rc;
