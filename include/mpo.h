@@ -157,9 +157,21 @@ int mpo_theta(mpo_handle h, int bond, const double *gate, double p, void *out, i
 
 /* Apply a general 16x16 two-site superoperator (row 4*I_l + I_{l+1}, column
  * 4*J_l + J_{l+1}, App. A convention), complex128 interleaved [16][16][2],
- * host pointer, on ABI bond b. Sec. 2.2 notes the method covers any
- * two-qubit error model; this entry takes the map directly. */
+ * host or device pointer, on ABI bond b. Sec. 2.2 notes the method covers
+ * any two-qubit error model; this entry takes the map directly. A map that
+ * mpo_check_superop rejects (tolerance 1e-9) returns MPO_ERR_ARG and leaves
+ * the state untouched. */
 int mpo_apply_superop(mpo_handle h, int bond, const double *M);
+
+/* Is M (as for mpo_apply_superop) a quantum channel (Sec. 2.2)? Checks trace
+ * preservation, t^T M = t^T with t the vectorised two-qubit trace (t_I = 1
+ * for I in {0, 3} on each qubit), and complete positivity, the 16x16 Choi
+ * matrix C[(a, j), (b, k)] = (M(|j><k|))_{ab} Hermitian positive
+ * semidefinite (host FP64 Jacobi eigenvalues), each to tol (<= 0: 1e-9)
+ * times the largest |M_ij|. Returns MPO_OK or MPO_ERR_ARG (MPO_ERR_CUDA if a
+ * device M cannot be read); *defect (may be NULL) receives the larger
+ * violation. Host code only: runs without a GPU for host M. */
+int mpo_check_superop(const double *M, double tol, double *defect);
 
 /* Run the Schmidt sweep now (normally done at the end of mpo_apply_layer). */
 int mpo_sweep(mpo_handle h);
@@ -353,8 +365,14 @@ int mpo_svd_last_stats(int *sweeps, double *phase_ms3);
  *
  *   - Larger matrices are rejected with MPO_ERR_ARG; mpo_last_error(NULL) says
  *     which limit was hit. Other errors as for mpo_svd.
- *   - The first call on a device looks up that array's device address with
- *     the device current; make that first call before any stream capture.
+ *   - The first call on a device loads the library's device code (CUDA loads
+ *     modules lazily by default) and maps the array, so that call itself
+ *     takes device memory (about 1.7 MB plus the module) and looks up the
+ *     array's address. Callers inside allocator hooks or under a fixed budget
+ *     make one warm-up call at initialisation (any size, e.g. 1 x 1), before
+ *     any stream capture; later calls allocate nothing.
+ *   - mpo_svd_last_stats reports the sweeps and phase times of the last call,
+ *     as for mpo_svd(..., block = 1).
  *   - All calls on a device share the one array, which keeps the last call's
  *     contents. Calls whose work overlaps on the GPU (several streams, several
  *     host threads) race on it and must be serialised by the caller.

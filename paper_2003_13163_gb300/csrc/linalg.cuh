@@ -593,39 +593,8 @@ __global__ void conj_transpose_kernel(const cplx<T>* __restrict__ in, int r, int
 }
 
 
-// ---------------------------------------------------------------------------
-// TMA bulk-copy staging (cp.async.bulk, global -> shared) with mbarrier
-// completion. Every wait is bounded; on expiry the error word is set.
-// ---------------------------------------------------------------------------
+// Shared-memory address of a generic pointer (for cp.async).
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_addr(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n"
-               :: "r"(smem_addr(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void tma_bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-               :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
-}
-
-// Wait for phase `parity` of bar; false if the wait exceeded timeout_ns.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long timeout_ns) {
-  unsigned long long t0 = 0;
-  for (long it = 0;; ++it) {
-    unsigned ok;
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-                 : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
-    if (ok) return true;
-    if (it == 0) t0 = global_timer_ns();
-    else if ((it & 255) == 0 && (long long)(global_timer_ns() - t0) > timeout_ns) return false;
-  }
-}
 
 // ---------------------------------------------------------------------------
 // Block one-sided Jacobi SVD (row blocks of JB rows; a pair holds 2 JB rows).

@@ -29,6 +29,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <cmath>
+#include <complex>
 #include <string>
 #include <vector>
 #include <algorithm>
@@ -1209,6 +1210,95 @@ static int chain_t(mpo_ctx* h, int S, const double* uniforms, unsigned char* bit
 }
 
 // ================================================================ C ABI ====
+// ------------------------------------------------------ map validation ----
+// Eigenvalues of an n x n Hermitian matrix (row-major complex, n <= 16) by
+// the cyclic Jacobi method in FP64 on the host (Golub & Van Loan, Sec. 8.5):
+// rotations until every off-diagonal entry is below 1e-15 of the Frobenius
+// norm. Returns the smallest eigenvalue.
+static double hermitian_min_eig(std::vector<std::complex<double>> A, int n) {
+  double fro = 0.0;
+  for (const auto& z : A) fro += std::norm(z);
+  fro = std::sqrt(fro);
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) off = std::max(off, std::abs(A[p * n + q]));
+    if (off <= 1e-15 * fro) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const std::complex<double> g = A[p * n + q];
+        const double ag = std::abs(g);
+        if (ag <= 1e-300) continue;
+        const double a = A[p * n + p].real(), b = A[q * n + q].real();
+        const double zeta = (b - a) / (2.0 * ag);
+        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), sn = t * c;
+        const std::complex<double> u = g / ag;
+        // J = [[c, s], [-conj(u) s, conj(u) c]] on columns p, q; A <- J^H A J
+        for (int k = 0; k < n; ++k) {          // A <- A J
+          const std::complex<double> x = A[k * n + p], y = A[k * n + q];
+          A[k * n + p] = c * x - sn * std::conj(u) * y;
+          A[k * n + q] = sn * x + c * std::conj(u) * y;
+        }
+        for (int k = 0; k < n; ++k) {          // A <- J^H A
+          const std::complex<double> x = A[p * n + k], y = A[q * n + k];
+          A[p * n + k] = c * x - sn * u * y;
+          A[q * n + k] = sn * x + c * u * y;
+        }
+        A[p * n + q] = A[q * n + p] = 0.0;
+      }
+  }
+  double mn = A[0].real();
+  for (int i = 1; i < n; ++i) mn = std::min(mn, A[i * n + i].real());
+  return mn;
+}
+
+// Checks a two-qubit superoperator M (App. A convention: row 4 I_l + I_r,
+// I = 2 ket + bra) for the two properties of a quantum channel (Sec. 2.2):
+// trace preservation, t^T M = t^T with t_I = 1 for I in {0, 3} on each qubit;
+// complete positivity, the Choi matrix C[(a, j), (b, k)] = (M(|j><k|))_{ab}
+// (two-qubit indices a, b, j, k = 2 q_l + q_r) positive semidefinite. The
+// tolerance is tol times the largest |M_ij|. Returns 0, 1 (not trace
+// preserving) or 2 (not completely positive); *defect receives the larger
+// violation (the largest |t^T M - t^T| entry or minus the smallest Choi
+// eigenvalue).
+static int check_superop(const std::complex<double>* M, double tol, double* defect) {
+  double mx = 0.0;
+  for (int e = 0; e < 256; ++e) mx = std::max(mx, std::abs(M[e]));
+  const double lim = tol * std::max(mx, 1e-300);
+  auto t = [](int I) { return (I == 0 || I == 3) ? 1.0 : 0.0; };
+  double tp = 0.0;
+  for (int col = 0; col < 16; ++col) {
+    std::complex<double> v = 0.0;
+    for (int row = 0; row < 16; ++row) v += t(row / 4) * t(row % 4) * M[row * 16 + col];
+    tp = std::max(tp, std::abs(v - t(col / 4) * t(col % 4)));
+  }
+  std::vector<std::complex<double>> C(256);
+  for (int a = 0; a < 4; ++a)
+    for (int j = 0; j < 4; ++j)
+      for (int b = 0; b < 4; ++b)
+        for (int k = 0; k < 4; ++k) {
+          const int row = 4 * (2 * (a >> 1) + (b >> 1)) + (2 * (a & 1) + (b & 1));
+          const int col = 4 * (2 * (j >> 1) + (k >> 1)) + (2 * (j & 1) + (k & 1));
+          C[(4 * a + j) * 16 + (4 * b + k)] = M[row * 16 + col];
+        }
+  // the Choi matrix of a Hermiticity-preserving map is Hermitian; use its
+  // Hermitian part and count the rest as a defect
+  double herm = 0.0;
+  for (int x = 0; x < 16; ++x)
+    for (int y = x; y < 16; ++y) {
+      herm = std::max(herm, std::abs(C[x * 16 + y] - std::conj(C[y * 16 + x])));
+      const std::complex<double> h = 0.5 * (C[x * 16 + y] + std::conj(C[y * 16 + x]));
+      C[x * 16 + y] = h;
+      C[y * 16 + x] = std::conj(h);
+    }
+  const double cp = std::max(herm, -hermitian_min_eig(C, 16));
+  if (defect) *defect = std::max(tp, cp);
+  if (tp > lim) return 1;
+  if (cp > lim) return 2;
+  return 0;
+}
+
 extern "C" {
 
 void mpo_default_opts(mpo_opts* o) {
@@ -1493,9 +1583,27 @@ int mpo_theta(mpo_handle h, int bond, const double* gate, double p, void* out, i
                   : theta_t<float>(h, bond, gate, p, out, rows, cols);
 }
 
+int mpo_check_superop(const double* M, double tol, double* defect) {
+  if (!M) return MPO_ERR_ARG;
+  std::complex<double> hm[256];
+  if (is_device_ptr(M)) {
+    if (cudaMemcpy(hm, M, sizeof(hm), cudaMemcpyDeviceToHost) != cudaSuccess) { cudaGetLastError(); return MPO_ERR_CUDA; }
+  } else {
+    std::memcpy(hm, M, sizeof(hm));
+  }
+  return check_superop(hm, tol > 0.0 ? tol : 1e-9, defect) ? MPO_ERR_ARG : MPO_OK;
+}
+
 int mpo_apply_superop(mpo_handle h, int bond, const double* M) {
   GUARD(h);
   if (bond < 0 || bond > h->n - 2 || !M) return fail(h, MPO_ERR_ARG, "bad bond or superoperator");
+  {
+    double defect = 0.0;
+    const int rc = mpo_check_superop(M, 1e-9, &defect);
+    if (rc == MPO_ERR_CUDA) return fail(h, rc, "could not read the superoperator");
+    if (rc) return fail(h, MPO_ERR_ARG, "superoperator is not trace preserving and completely positive (defect " +
+                                            std::to_string(defect) + ")");
+  }
   const double2* src = (const double2*)M;
   if (!is_device_ptr(M)) {
     CK(h, cudaMemcpyAsync(h->dsup, M, sizeof(double2) * 256, cudaMemcpyHostToDevice, h->st));
@@ -1866,12 +1974,15 @@ int mpo_svd_static(int r, int c, void* X, void* w, void* Ut, mpo_precision prec,
       : launch_block_jacobi<float>(st, (float2*)X, r, c, c, (float2*)Ut, (float*)w, (float2*)s->gpart,
                                    kStaticSlots, (float2*)s->jbuf, s->act, bj_state_ints(kStaticMaxRows), &s->ctl,
                                    ms, 5.0, sms);
-  GridCtl hc{};
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, &s->ctl.g, sizeof(GridCtl), cudaMemcpyDeviceToHost, st);
+  OSCtl hctl{};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hctl, &s->ctl, sizeof(OSCtl), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) { g_last_init_error = cudaGetErrorString(e); return MPO_ERR_CUDA; }
-  if (hc.err) return MPO_ERR_TIMEOUT;
-  if (hc.status) return MPO_ERR_NOCONV;
+  // the same statistics as mpo_svd(..., block = 1) for mpo_svd_last_stats
+  g_last_svd_sweeps = hctl.g.sweeps;
+  for (int i = 0; i < 3; ++i) g_last_svd_phase_ms[i] = 1e-6 * (double)hctl.phase_ns[i];
+  if (hctl.g.err) return MPO_ERR_TIMEOUT;
+  if (hctl.g.status) return MPO_ERR_NOCONV;
   return MPO_OK;
 }
 

@@ -24,7 +24,7 @@ EXPORTS = ["mpo_default_opts", "mpo_init", "mpo_apply_layer", "mpo_apply_gate", 
            "mpo_profile", "mpo_profile_read", "mpo_profile_sweeps", "mpo_profile_steps", "mpo_profile_phases", "mpo_svd_static",
            "mpo_probability", "mpo_sample", "mpo_gemm", "mpo_svd_last_stats",
            "mpo_init_batch", "mpo_apply_layer_batch", "mpo_batch_instance", "mpo_svd_truncated", "mpo_gemm_ex",
-           "mpo_theta"]
+           "mpo_theta", "mpo_check_superop"]
 
 
 class MPOError(RuntimeError):
@@ -89,6 +89,7 @@ def load_library(path: str | None = None):
         "mpo_svd_truncated": (I, [I, I, P, I, I, ctypes.POINTER(Opts), P, P, DP, IP, P]),
         "mpo_gemm_ex": (I, [I, I, I, P, I, I, P, I, I, P, I, I, I, P]),
         "mpo_theta": (I, [P, I, P, D, P, IP, IP]),
+        "mpo_check_superop": (I, [P, D, DP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -475,6 +476,18 @@ def svd_truncated(A, cap: int, precision: str = "mixed", **opts):
         raise MPOError(rc, lib.mpo_last_error(None).decode())
     kk = k.value
     return U[:, :kk], X[:kk], lam2[:kk]
+
+
+def check_superop(M, tol: float = 0.0):
+    """(is_channel, defect) of a 16x16 two-qubit superoperator in the App. A
+    convention (mpo_check_superop): trace preserving and completely positive
+    to tol times its largest entry."""
+    M = np.ascontiguousarray(M, dtype=np.complex128)
+    d = ctypes.c_double()
+    rc = load_library().mpo_check_superop(_ptr(M), float(tol), ctypes.byref(d))
+    if rc not in (0, -1):
+        raise MPOError(rc, "mpo_check_superop failed")
+    return rc == 0, d.value
 
 
 def gemm_ex(A, B, opA: int = 0, opB: int = 0, precision: str = "fp64", engine: int = 1):

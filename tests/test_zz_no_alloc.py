@@ -57,3 +57,51 @@ def test_static_scratch_svd_rejects_oversize(M):
     with pytest.raises(M.MPOError) as e:
         M.svd_rows_static(X, "fp64")
     assert e.value.code == -1 and "scratch limit" in str(e.value)
+
+
+@pytest.mark.parametrize("r,c", [(512, 2048), (512, 1537)])
+def test_static_scratch_svd_at_the_limit(M, r, c):
+    """At the built-in limit (512 rows, 2048 columns), where the pair and
+    chunk counts fill the static array exactly, and with a ragged last
+    column chunk: the same factorisation as the allocating entry point."""
+    import torch
+    X = torch.tensor(_matrix(r, c, 11), dtype=torch.complex128, device="cuda")
+    Xa, Xs = X.clone(), X.clone()
+    wa, Ua = M.svd_rows(Xa, "fp64", block=True)
+    ws, Us = M.svd_rows_static(Xs, "fp64")
+    tol = 50 * 2.2e-16 * np.sqrt(c)
+    np.testing.assert_allclose(Xs.cpu().numpy(), Xa.cpu().numpy(), atol=tol)
+    np.testing.assert_allclose(Us.cpu().numpy(), Ua.cpu().numpy(), atol=tol)
+    np.testing.assert_allclose(ws.cpu().numpy(), wa.cpu().numpy(), rtol=1e-12, atol=1e-14)
+
+
+def test_static_scratch_svd_rejects_oversize_columns(M):
+    import torch
+    X = torch.zeros((64, 2049), dtype=torch.complex128, device="cuda")
+    with pytest.raises(M.MPOError) as e:
+        M.svd_rows_static(X, "fp64")
+    assert e.value.code == -1 and "scratch limit" in str(e.value)
+
+
+def test_static_scratch_svd_allocates_nothing_after_warm_up(M):
+    """After a first call (which loads the module and maps the array), a call
+    leaves the free device memory unchanged and updates the statistics that
+    mpo_svd_last_stats reports."""
+    import ctypes
+    import torch
+    lib = M.load_library()
+    X0 = torch.tensor(_matrix(8, 16, 3), dtype=torch.complex128, device="cuda")
+    M.svd_rows_static(X0.clone(), "fp64")                       # warm-up
+    r, c = 300, 900
+    X = torch.tensor(_matrix(r, c, 5), dtype=torch.complex128, device="cuda")
+    w = torch.empty(r, dtype=torch.float64, device="cuda")
+    Ut = torch.empty((r, r), dtype=torch.complex128, device="cuda")
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    rc = lib.mpo_svd_static(r, c, X.data_ptr(), w.data_ptr(), Ut.data_ptr(), M.MPO_FP64, 0, st)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert rc == 0 and free1 == free0
+    stats = M.svd_last_stats()
+    assert stats["sweeps"] > 0 and stats["gram_ms"] + stats["pair_eig_ms"] + stats["apply_ms"] > 0
