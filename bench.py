@@ -55,6 +55,11 @@ METRIC = "noisy-gate MPO updates/s at chi=1024 (mixed vs FP64, |dS|<=1e-6); % ro
 # the measured peaks file carries only the HBM copy and the BF16 GEMM rates.
 FP64_PROBE_TFLOPS = 1.20
 FP32_PROBE_TFLOPS = 74.6
+# DRAM bytes (read + written) per algorithmic flop of the split-BF16 GEMM,
+# from an ncu capture of one 4096 x 2048 x 4096 complex product
+# (dram__bytes_read.sum + dram__bytes_write.sum = 6.418e9 B for 2.749e11 flop);
+# the traffic of an average launch scales with its flops
+OZ_DRAM_BYTES_PER_FLOP = 6.418e9 / 2.749e11
 
 
 def load_peaks() -> dict:
@@ -521,8 +526,11 @@ def run_single(args, wl, prec) -> None:
     else:
         bound, pk, unit, basis = "hbm", peaks["hbm_gbs"], "GB/s", f"HBM copy ({peaks['source']})"
         achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
+    traffic = OZ_DRAM_BYTES_PER_FLOP * d["flops"] / d["launches"] if dom == "oz_gemm" else None
     roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": pk, "unit": unit,
-                "frac": achieved / pk, "traffic": None, "peak_basis": basis,
+                "frac": achieved / pk, "traffic": traffic, "peak_basis": basis,
+                "traffic_basis": "ncu dram bytes of one 4096 x 2048 x 4096 launch, scaled by flops"
+                if traffic is not None else None,
                 "share_of_step": d["ms"] / ms, "launches": d["launches"], "avg_launch_ms": d["ms"] / d["launches"]}
     p_gemm = peaks["fp64_tflops"] if prec == "fp64" else peaks["tf32_tflops"]
     p_solve = peaks["fp32_simt_tflops"] if prec == "fp32" else peaks["fp64_tflops"]
