@@ -400,7 +400,8 @@ def run_single(args, wl, prec) -> None:
     from paper_2003_13163_gb300.circuits import random_circuit
 
     n, chi, p = wl["n"], wl["chi"], wl["p"]
-    centre_only = args.centre_only or wl.get("centre_only", False)
+    # App. A's schedule sweeps the whole chain (every bond) after every gate
+    centre_only = (args.centre_only or wl.get("centre_only", False)) and args.update == "local"
     R = ramp_layers(n, chi)
     K, W = args.steps, args.warmup
     per_layer = n // 2 - 0.5
@@ -421,11 +422,13 @@ def run_single(args, wl, prec) -> None:
     torch.cuda.synchronize()
     t_ramp = time.perf_counter() - t_ramp0
 
+    global_update = args.update == "global"
+
     def step(entry, bufs, read_back):
         t, g, b, last = entry
         m.apply_gate(b, bufs[(t, g)], float(circ.p[t - 1][g]))
         d2h = 0
-        if last:
+        if last or global_update:      # App. A's schedule re-canonicalises after every gate
             m.sweep()
             if read_back:
                 S, _, _ = m.entropy(with_trace=False)
@@ -472,7 +475,7 @@ def run_single(args, wl, prec) -> None:
     for t, g, b, last in timed:
         for key, v in gate_work(dims, b, chi, prec).items():
             work[key] += v
-        if last:
+        if last or global_update:
             for key, v in sweep_work(dims, n, centre_only).items():
                 work[key] += v
 
@@ -549,8 +552,10 @@ def run_single(args, wl, prec) -> None:
             "dtype": {"fp32": "f32", "fp64": "f64", "mixed": "f64 (FP32 solves + split-BF16 products)"}[prec],
             "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "chi_max": chi, "p": p, "seed": wl["seed"],
-                       "precision": prec, "step": "one noisy gate (a2-a6); the end-of-step sweep and entropy "
-                       "with the step's last gate", "entropy": "centre bond" if centre_only else "every bond",
+                       "precision": prec, "update": args.update,
+                       "step": "one noisy gate (a2-a6); the end-of-step sweep and entropy with the step's last gate"
+                       if args.update == "local" else "one noisy gate followed by a sweep of the whole chain (App. A)",
+                       "entropy": "centre bond" if centre_only else "every bond",
                        "parallelism": f"replicas{world}", "ramp_layers": R, "ramp_seconds": round(t_ramp, 2),
                        "warmup_gates": W, "timed_gates": K, "layer_ends_timed": layers_timed,
                        "max_bond_dim": int(max(dims)), "bond_dims_min_centre": int(min(dims[n // 4: 3 * n // 4])),
@@ -593,6 +598,9 @@ def main():
     ap.add_argument("--centre-only", action="store_true", help="record S at the centre bond only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the precision form's FP64 comparisons")
+    ap.add_argument("--update", default="local", choices=["local", "global"],
+                    help="local: one sweep per brickwork step (the engine's schedule); global: App. A's "
+                         "re-canonicalisation of the whole chain after every gate (timed comparator)")
     ap.add_argument("--workers", type=int, default=8, help="host worker threads of the batching form")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
