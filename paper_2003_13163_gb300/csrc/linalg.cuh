@@ -384,33 +384,6 @@ __global__ void __launch_bounds__(1024) select_kernel(const T* __restrict__ w, i
 }
 
 // ---------------------------------------------------------------------------
-// Gather selected eigenvector columns with a per-column scale.
-//   transpose_conj == 0: out[r*ldo + j] = V[r*ldv + perm[j]] * f_j
-//   transpose_conj == 1: out[j*ldo + r] = conj(V[r*ldv + perm[j]]) * f_j
-// f_j by mode: 0 -> 1; 1 -> 1/sqrt(lam2_j); 2 -> sqrt(lam2_j / kept);
-//              3 -> sqrt(lam2_j).
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void gather_kernel(const cplx<T>* __restrict__ V, int ldv, const int* __restrict__ perm,
-                              const double* __restrict__ lam2, const SelectInfo* __restrict__ info,
-                              int rows, int k_cap, int transpose_conj, int mode, cplx<T>* __restrict__ out, int ldo) {
-  const int k = info->k < k_cap ? info->k : k_cap;
-  const size_t total = (size_t)rows * k;
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    int r, j;
-    if (transpose_conj) { j = (int)(e / rows); r = (int)(e % rows); }
-    else { r = (int)(e / k); j = (int)(e % k); }
-    double f = 1.0;
-    if (mode == 1) f = lam2[j] > 0.0 ? 1.0 / sqrt(lam2[j]) : 0.0;
-    else if (mode == 2) f = info->kept > 0.0 ? sqrt(lam2[j] / info->kept) : 0.0;
-    else if (mode == 3) f = sqrt(lam2[j]);
-    cplx<T> v = V[(size_t)r * ldv + perm[j]];
-    if (transpose_conj) out[(size_t)j * ldo + r] = cscale<T>(cconj<T>(v), (T)f);
-    else out[(size_t)r * ldo + j] = cscale<T>(v, (T)f);
-  }
-}
-
-// ---------------------------------------------------------------------------
 // One-sided (Hestenes) Jacobi SVD by row orthogonalisation.
 // Input X (r x c, row-major, leading dimension ldx), in place. On exit the
 // rows of X are mutually orthogonal, X_out = U^H X_in with U unitary (r x r),

@@ -174,25 +174,6 @@ __global__ void gauss_start_kernel(double2* __restrict__ out, size_t n, unsigned
   }
 }
 
-// G (m x m) diagonal += rel * trace(G) (the shift of shifted Cholesky QR).
-// One CTA.
-__global__ void add_trace_shift_kernel(double2* __restrict__ G, int m, double rel) {
-  __shared__ double red[32];
-  double s = 0.0;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) s += G[(size_t)i * m + i].x;
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double v = 0.0;
-    for (int i = 0; i < (blockDim.x + 31) / 32; ++i) v += red[i];
-    red[0] = v;
-  }
-  __syncthreads();
-  const double sh = rel * red[0];
-  for (int i = threadIdx.x; i < m; i += blockDim.x) G[(size_t)i * m + i].x += sh;
-}
-
 // *out += sum |A_ij|^2 over an r x c complex128 matrix (leading dimension
 // lda), accumulated in FP64: grid-stride partial sums, one atomicAdd per CTA
 // (*out zeroed beforehand).

@@ -101,14 +101,6 @@ __global__ void trace_step_kernel(const cplx<T>* __restrict__ A, int chiL, int c
   vout[c] = make_double2(re, im);
 }
 
-// Scale a complex array in place by a device FP64 scalar (or its reciprocal).
-template <typename T>
-__global__ void scale_kernel(cplx<T>* __restrict__ x, size_t n, const double* __restrict__ s, int reciprocal) {
-  const double f = reciprocal ? 1.0 / *s : *s;
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
-    x[e] = cscale<T>(x[e], (T)f);
-}
-
 // ---------------------------------------------------------------------------
 // Right trace environments (Sec. 3.4): R_k[a] = sum_c (A_k[a,0,c] + A_k[a,3,c]) R_{k+1}[c],
 // R_n = (1): the contraction of sites k..n-1 with the vectorised identity.
